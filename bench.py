@@ -1,0 +1,354 @@
+#!/usr/bin/env python3
+"""Trotter steps/s and HBM roofline of the 27-qubit gauge-Higgs evolution on GB300.
+
+Workload: 3x3 periodic gauge-Higgs lattice (18 link + 9 vertex = 27 qubits),
+complex64 state (1.07 GB, larger than L2), H(s) = (1-s) H0 + s H1 with
+J = h = 1, (g, lambda) = (0.6, 0.6), linear ramp over T = 20 in 1000 second-order
+Trotter steps (dt = 0.02); the timed steps are a window of that schedule.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  `value` = Trotter steps/s over all ranks (each rank
+evolves its own replica: the single-state path does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(name="gh3x3_27q_c64_fused_order2", Lx=3, Ly=3, form="gh", dtype="c64",
+                g=0.6, lam=0.6, T=20.0, total_steps=1000, order=2)
+METRIC = "trotter_steps_per_sec"
+UNIT = "steps/s"
+
+
+def linear_midpoints(T, n):
+    # s_k = t_k / T at t_k = (k - 1/2) dt: a schedule input, computed identically by the oracle
+    dt = T / n
+    return (np.arange(1, n + 1) - 0.5) * dt / T
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(kernel_tag: str):
+    """dram read+write bytes per launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
+    if not os.path.exists(path):
+        return None
+    src = open(os.path.join(ROOT, "paper_2108_13410_gb300", "csrc", "kernels.cuh"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernels_cuh_sha256_16") != h:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND") != "gloo" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(budget_s: float, max_steps: float = 1e9):
+    """Time the FP64 oracle on the 27-qubit workload for about budget_s seconds.
+
+    The oracle applies the Trotter step factor by factor (81 Pauli factors per
+    second-order step at 27 qubits); a bounded sample is a run of whole factors,
+    scaled to steps.  Returns (steps_per_s, cores, description)."""
+    from oracle import OracleLattice, Couplings
+    from oracle import core as O
+    lat = OracleLattice(WORKLOAD["Lx"], WORKLOAD["Ly"], True, WORKLOAD["form"])
+    c = Couplings(WORKLOAD["g"], WORKLOAD["lam"])
+    n = lat.n_qubits
+    dt = WORKLOAD["T"] / WORKLOAD["total_steps"]
+    s = linear_midpoints(WORKLOAD["T"], WORKLOAD["total_steps"])
+    psi = O.plus_state(n)
+    xs, zs = O._terms(lat)
+    factors = []                                    # one second-order step: X/2, Z, X/2
+    coef = O.coefficients(c, float(s[0]))
+    factors += [(k, t, coef[key] * 0.5 * dt) for k, t, key in xs]
+    factors += [(k, t, coef[key] * dt) for k, t, key in zs]
+    factors += [(k, t, coef[key] * 0.5 * dt) for k, t, key in xs]
+    per_step = len(factors)
+    done = 0
+    t0 = time.perf_counter()
+    while True:
+        k, tgt, th = factors[done % per_step]
+        O._apply(psi, n, k, tgt, th)
+        done += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or done >= max_steps * per_step:
+            break
+    steps = done / per_step
+    return steps / el, O.max_threads(), (f"{done} Pauli factors ({steps:.3f} second-order steps) of the "
+                                         f"27-qubit workload, FP64, {el:.1f} s")
+
+
+def run_reference(args):
+    world, rank, local = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    # warm-up: one factor-sized sample per warm-up step
+    budget_total = 150.0
+    per = budget_total / max(1, args.steps + args.warmup)
+    oracle_sample(min(per, 2.0))
+    rates, descs = [], []
+    for _ in range(args.steps):
+        r, cores, d = oracle_sample(per)
+        rates.append(r)
+        descs.append(d)
+    value = float(np.mean(rates))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD["name"], "qubits": 27},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"each step: {descs[-1]}"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2108_13410_gb300 import Simulator, QS_OPT_PROFILE
+    from paper_2108_13410_gb300 import qsim as Q
+
+    W = WORKLOAD
+    dt = W["T"] / W["total_steps"]
+    sched = linear_midpoints(W["T"], W["total_steps"])
+    K, Wu = args.steps, args.warmup
+    assert K + Wu <= W["total_steps"], "steps + warmup must fit the 1000-step schedule"
+    cpl = [(W["g"], W["lam"])]
+    sim = Simulator(W["Lx"], W["Ly"], form=W["form"], dtype=W["dtype"], device=f"cuda:{local}")
+    stream = torch.cuda.current_stream(dev)
+    sim.init_plus()
+    # warm-up
+    sim.evolve(cpl, sched[:Wu], dt, W["order"])
+    torch.cuda.synchronize(dev)
+    sim.set_option(QS_OPT_PROFILE, 1)
+    sim.profile_read()
+    sim.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.evolve(cpl, sched[Wu:Wu + K], dt, W["order"])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    launches = sim.launch_count()
+    xpass_ms, xpass_n = sim.profile_read()
+    sim.set_option(QS_OPT_PROFILE, 0)
+    ms_max = max_over_ranks(world, ms, dev)
+    value = world * K / (ms_max / 1000.0)
+
+    state_bytes = sim.state_bytes
+    alg_bytes = 2.0 * state_bytes                     # one read + one write of the state per pass
+    avg_ms = xpass_ms / max(1, xpass_n)
+    achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
+    peak, peak_kind = peaks()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profile_traffic("k_xpass_c64_27q"),
+                "kernel": "k_xpass<float>", "launches": xpass_n, "avg_launch_ms": avg_ms,
+                "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
+                "step_hbm_gbs": (xpass_n / K) * alg_bytes / (ms / K / 1000.0) / 1e9}
+
+    # ---- end to end through the public API with host buffers ----
+    host_state = torch.empty(sim.state.shape, dtype=sim.state.dtype, pin_memory=True)
+    host_state[0].fill_(2 ** (-sim.n / 2))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    sim.upload(host_state)                                   # h2d: initial state
+    sim.evolve(cpl, sched[Wu:Wu + K], dt, W["order"])        # h2d: per-step operator records
+    e_fin = sim.energy(cpl)                                  # d2h: reduction records
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(world, e2e_s, dev)
+    rec_bytes = (4 + 2 * 10 * 19) * 8                        # doubles per operator record (3x3)
+    e2e = {"value": world * K / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": (state_bytes + (K + 1) * rec_bytes) / K,
+           "d2h_bytes_per_step": (1 + sim.n) * 4 * 8 / K,
+           "final_energy": float(e_fin[0])}
+
+    extra = {}
+    if rank == 0 and not args.no_pergate:
+        # the plain complex128 per-gate form on the same GPU, a few steps
+        del host_state
+        torch.cuda.empty_cache()
+        sp = Simulator(W["Lx"], W["Ly"], form=W["form"], dtype="c128", device=f"cuda:{local}", method="pergate")
+        sp.init_plus()
+        sp.evolve(cpl, sched[:1], dt, W["order"])
+        torch.cuda.synchronize(dev)
+        kp = 3
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        sp.evolve(cpl, sched[1:1 + kp], dt, W["order"])
+        a1.record(stream)
+        torch.cuda.synchronize(dev)
+        pg = kp / (a0.elapsed_time(a1) / 1000.0)
+        extra["pergate_c128"] = {"value": pg, "unit": UNIT, "steps": kp,
+                                 "fused_c64_speedup": value / world / pg}
+        del sp
+        torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        r, cores, desc = oracle_sample(args.cpu_budget)
+        cpu = {"value": r, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+               "warmup": Wu, "ms_per_step": ms_max / K, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+               "config": {"workload": W["name"], "lattice": "3x3 periodic", "form": "gauge-Higgs",
+                          "qubits": 27, "g": W["g"], "lambda": W["lam"], "J": 1.0, "h": 1.0,
+                          "T": W["T"], "dt": dt, "order": W["order"], "state_bytes": state_bytes,
+                          "l2": "inputs larger than L2 (1.07 GB state, 129 MB L2)",
+                          "parallelism": "replicas" if world > 1 else "single"},
+               "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+               "clocks": clk}
+        out.update(extra)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-pergate", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,150 @@
+/*
+ * qsim.h -- C ABI of the GB300 state-vector engine for the Trotterised adiabatic
+ * evolution of the Z2 gauge-Higgs model (Ding, Cui, Shi, "Digital quantum
+ * simulation and pseudoquantum simulation of the Z2 gauge-Higgs model").
+ *
+ * Model (Sec. II).  Gauge-Higgs form, Eq. (1):
+ *     H1 = -J sum_v tau^x_v - h sum_p B_p - g sum_l sigma^x_l
+ *          - lambda sum_<jk> tau^z_j sigma^z_<jk> tau^z_k,   B_p = prod_{l in p} sigma^z_l.
+ * Unitary-gauge (toric code in two transverse fields) form, Eq. (4):
+ *     H1 = -J sum_v A_v - h sum_p B_p - g sum_l sigma^x_l - lambda sum_l sigma^z_l,
+ *     A_v = prod_{l at v} sigma^x_l.
+ * Adiabatic path (Sec. III): H(s) = (1 - s) H0 + s H1 with H0 = -sum of the X-type
+ * fields (-sum sigma^x - sum tau^x, or -sum sigma^x - sum A_v), ground state |+>^n.
+ * Trotter product (Eq. (7), Eq. (8)), operators acting right to left:
+ *     order 1:  U = exp(-i dt H_Z) exp(-i dt H_X)
+ *     order 2:  U = exp(-i dt/2 H_X) exp(-i dt H_Z) exp(-i dt/2 H_X)
+ * where H_X collects sigma^x, tau^x, A_v and H_Z collects B_p, the bonds and sigma^z.
+ *
+ * Qubit numbering (periodic Lx x Ly torus, N = Lx*Ly vertices, v = y*Lx + x):
+ *     horizontal link (x,y)->(x+1,y): qubit v;  vertical link (x,y)->(x,y+1): N + v;
+ *     vertex tau_v (gauge-Higgs only): 2N + v.
+ * Open boundary: Lx x Ly plaquettes, (Lx+1) x (Ly+1) vertices; the existing
+ * horizontal links in vertex order, then the vertical links, then the vertices.
+ * Plaquette (x,y) = {h(x,y), h(x,y+1), u(x,y), u(x+1,y)}; star A_v = the existing
+ * links among {h(x,y), h(x-1,y), u(x,y), u(x,y-1)}.  Bit value 0 is Z = +1.
+ *
+ * State layout.  `batch` state vectors of 2^n amplitudes, back to back; amplitude
+ * i of state b at element b * 2^n + i, stored as interleaved (re, im) float
+ * (QS_C64) or double (QS_C128).  State memory is allocated by the caller (e.g.
+ * PyTorch) and borrowed through qs_bind_state; the library never frees it.
+ *
+ * Conventions.  Every call returns a qs_status; on error no output is written
+ * and qs_last_error() describes the failure.  Host pointers belong to the
+ * caller.  All device work is stream-ordered on the stream given to
+ * qs_set_stream (default: the legacy default stream).  Calls that return host
+ * scalars synchronise that stream.  A qs_sim is not thread-safe.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qs_sim qs_sim;
+
+typedef enum {
+    QS_OK = 0,
+    QS_ERR_ARG = 1,        /* invalid argument (null pointer, size, index, range) */
+    QS_ERR_OOM = 2,        /* library workspace allocation failed */
+    QS_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    QS_ERR_NONFINITE = 4,  /* a reduction produced NaN/Inf (e.g. a poisoned state) */
+    QS_ERR_TIMEOUT = 5,    /* a bounded device-side wait gave up */
+    QS_ERR_STATE = 6       /* call out of order (e.g. no state bound) */
+} qs_status;
+
+typedef enum { QS_PERIODIC = 0, QS_OPEN = 1 } qs_boundary;
+typedef enum { QS_GAUGE_HIGGS = 0, QS_UNITARY_GAUGE = 1 } qs_form;
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+/* Observables for qs_expect (Sec. II, Sec. IV). */
+typedef enum {
+    QS_NORM = 0,       /* <psi|psi>                                                  */
+    QS_PLAQUETTE = 1,  /* <B_p>, index = p; index = -1: average over all plaquettes  */
+    QS_WILSON = 2,     /* non-contractible Wilson loop: index 0 = W_x (links h(x,0)),
+                          index 1 = W_y (links u(0,y)); periodic lattices only       */
+    QS_X = 3,          /* <X_q>, index = qubit q                                      */
+    QS_ENERGY = 4,     /* <H1> with the given couplings (s ignored)                   */
+    QS_ENERGY_S = 5,   /* <H(s)> = (1-s)<H0> + s<H1>                                  */
+    QS_GAUSS = 6,      /* <Q_v> = <tau^x_v A_v>, index = v (gauge-Higgs form only)    */
+    QS_THOOFT = 7      /* 't Hooft loop: index 0 = prod_y X_h(0,y), 1 = prod_x X_u(x,0) */
+} qs_obs;
+
+/* Couplings of H1 (Eq. (1) / Eq. (4)); one record per batch element. */
+typedef struct { double J, h, g, lambda; } qs_couplings;
+
+/* Options for qs_set_option. */
+typedef enum {
+    QS_OPT_METHOD = 0,        /* 0: fused kernels (default); 1: one launch per Pauli
+                                 term (the plain per-gate form)                      */
+    QS_OPT_RENORM_EVERY = 1,  /* qs_evolve rescales the state to unit FP64 norm every
+                                 this many steps and at the end (0 = never; default 0) */
+    QS_OPT_PROFILE = 2,       /* 1: time every fused X-pass launch with CUDA events on
+                                 the bound stream (read with qs_profile_read)        */
+    QS_OPT_GRAPH = 3          /* 1: qs_evolve replays its launches as a CUDA graph    */
+} qs_option;
+
+/* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open
+ * needs Lx, Ly >= 1.  batch >= 1 independent states share the lattice; each has
+ * its own couplings.  Fails with QS_ERR_ARG if the qubit count exceeds 34.
+ * Allocates only small device workspaces (term tables, partial sums). */
+qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch,
+                    qs_sim **out);
+void qs_destroy(qs_sim *sim);
+/* Last error message of sim (or of the last failed qs_create when sim is NULL). */
+const char *qs_last_error(const qs_sim *sim);
+
+int qs_num_qubits(const qs_sim *sim);
+/* Bytes of all batch states (batch * 2^n * 8 or 16). */
+size_t qs_state_bytes(const qs_sim *sim);
+
+/* Borrow device memory: slot 0 = the evolved state psi, slot 1 = the adjoint
+ * work state (qs_adjoint_grad).  bytes must be >= qs_state_bytes and dev_ptr
+ * 256-byte aligned. */
+qs_status qs_bind_state(qs_sim *sim, int slot, void *dev_ptr, size_t bytes);
+/* cudaStream_t passed as void*; NULL = legacy default stream. */
+qs_status qs_set_stream(qs_sim *sim, void *stream);
+qs_status qs_set_option(qs_sim *sim, int key, long long value);
+
+/* psi <- |+>^n for every batch element (ground state of H0). */
+qs_status qs_init_plus(qs_sim *sim);
+/* Copy batch states between host memory (pinned for asynchronous transfer) and
+ * the bound state; bytes must equal qs_state_bytes.  Synchronises the stream. */
+qs_status qs_upload_state(qs_sim *sim, const void *host, size_t bytes);
+qs_status qs_download_state(qs_sim *sim, void *host, size_t bytes);
+
+/* One Trotter step of H(s) over time dt (order 1 or 2), couplings[batch]. */
+qs_status qs_trotter_step(qs_sim *sim, const qs_couplings *couplings, double s,
+                          double dt, int order);
+
+/* n_steps Trotter steps with s[k] (host array, the schedule at the midpoint of
+ * step k).  Second order merges the adjacent X half-steps of consecutive steps
+ * (the X-type terms commute), which leaves the product unchanged. */
+qs_status qs_evolve(qs_sim *sim, const qs_couplings *couplings, const double *s,
+                    double dt, int n_steps, int order);
+
+/* Expectation value per batch element, accumulated in FP64 (out: host [batch]).
+ * couplings and s are used by QS_ENERGY / QS_ENERGY_S only (may be NULL else). */
+qs_status qs_expect(qs_sim *sim, int kind, int index, const qs_couplings *couplings,
+                    double s, double *out);
+/* <psi|P|psi> for a Pauli string of one type: type 0 = Z string, 1 = X string,
+ * on the qubits set in mask (out: host [batch]). */
+qs_status qs_expect_pauli(qs_sim *sim, int type, uint64_t mask, double *out);
+/* |<phi|psi>|^2 per batch element; ref_dev_state has the layout of the bound
+ * state (same dtype, batch and size). out: host [batch]. */
+qs_status qs_fidelity(qs_sim *sim, const void *ref_dev_state, double *out);
+
+/* Total milliseconds and launch count of the fused X-pass kernel since the last
+ * read, when QS_OPT_PROFILE is on.  Synchronises the stream. */
+qs_status qs_profile_read(qs_sim *sim, double *total_ms, long long *launches);
+/* Number of kernels this library launched since the last call (all kinds). */
+long long qs_launch_count(qs_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

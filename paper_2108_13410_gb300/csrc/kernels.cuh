@@ -1,0 +1,428 @@
+// kernels.cuh -- sm_103a kernels of the Trotterised gauge-Higgs evolution.
+//
+// The hot path is a memory-bound butterfly over a 2^n-amplitude state vector:
+//   * k_xpass   : exp(i theta_q X_q) on up to 12 qubits per HBM pass.  A CTA stages
+//                 a 4096-amplitude tile (12 "local" bits chosen by the pass plan),
+//                 applies 4 qubits per register stage (radix-16 butterflies in
+//                 registers), transposes through shared memory between stages, and
+//                 optionally applies the whole diagonal Z layer before storing
+//                 (Eq. (8): all X-type factors commute, all Z-type factors commute).
+//   * k_zdiag   : the Z layer alone: amplitude i gets exp(i dt s [h sum_p (-1)^{pi_p(i)}
+//                 + lambda sum_b (-1)^{pi_b(i)}]), looked up from an FP64-built table
+//                 indexed by the number of odd plaquettes and odd bonds of i.
+//   * k_rx / k_zterm / k_xstring : one Pauli factor per launch (per-gate form).
+//   * k_reduce_* / k_finish : FP64 block partials and a fixed-order final sum.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qsim {
+
+constexpr int LT = 12;                 // tile bits (4096 amplitudes per CTA)
+constexpr int RB = 4;                  // register bits per stage (16 amplitudes / thread)
+constexpr int TB = LT - RB;            // thread bits
+constexpr int NT = 1 << TB;            // 256 threads per CTA
+constexpr int NR = 1 << RB;            // 16 registers (amplitudes) per thread
+constexpr int MAXQ = 40;
+constexpr int RED_THREADS = 256;
+constexpr int RED_NV = 4;              // values per reduction record
+
+// Fixed stage layouts (local bit -> register or thread):
+//   stage 0: registers = local {8..11}, threads = local {0..7}       (global load)
+//   stage 1: registers = local {0..3},  threads = local {4..11}      (shared memory)
+//   stage 2: registers = local {4..7},  threads = local {0..3, 8..11} (global store)
+struct PassDesc {
+    int n;                      // qubits
+    int nfixed;                 // n - LT tile-index bits
+    int fixed_pos[MAXQ];        // global bit of tile-index bit k (increasing)
+    int lmap[LT];               // global bit of local bit j
+    int stage1_on;              // stage 1 has something to rotate
+    unsigned rot_mask[3];       // per stage: register bits to rotate
+    int reg_cls[3][RB];         // X class (0 link sigma^x, 1 vertex tau^x) per register bit
+    int apply_z;                // multiply by the Z-layer phase before the store
+    int nA, nB;                 // Z class sizes (table is (nA+1) x (nB+1))
+    uint32_t colA[MAXQ];        // per global qubit: plaquettes containing it (bit p)
+    uint32_t colB[MAXQ];        // per global qubit: bonds / sigma^z terms containing it
+};
+
+// Operator record (doubles): [cos_sigma, sin_sigma, cos_tau, sin_tau,
+//   then (nA+1)(nB+1) complex phases exp(i phi(nA_odd, nB_odd)) as (re, im)].
+__host__ __device__ inline int record_doubles(int nA, int nB) {
+    int r = 4 + 2 * (nA + 1) * (nB + 1);
+    return (r + 1) & ~1;
+}
+
+template <typename R> struct C2;
+template <> struct C2<float> { using T = float2; };
+template <> struct C2<double> { using T = double2; };
+
+template <typename R>
+__device__ __forceinline__ typename C2<R>::T mk(R x, R y) {
+    typename C2<R>::T v; v.x = x; v.y = y; return v;
+}
+
+// (a, b) <- exp(i theta X) (a, b):  a' = c a + i s b,  b' = i s a + c b
+template <typename V, typename R>
+__device__ __forceinline__ void xrot(V &a, V &b, R c, R s) {
+    R ar = a.x, ai = a.y, br = b.x, bi = b.y;
+    a.x = c * ar - s * bi; a.y = c * ai + s * br;
+    b.x = c * br - s * ai; b.y = c * bi + s * ar;
+}
+
+template <typename V>
+__device__ __forceinline__ V cmul(V a, V b) {
+    V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+
+__device__ __forceinline__ int swz(int l) { return l ^ ((l >> 4) & 15); }
+
+template <typename R, typename V>
+__device__ __forceinline__ void rotate_regs(V (&v)[NR], unsigned mask, const int (&cls)[RB],
+                                            R c0, R s0, R c1, R s1) {
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+        R c = cls[k] ? c1 : c0;
+        R s = cls[k] ? s1 : s0;
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (!((r >> k) & 1)) xrot(v[r], v[r | (1 << k)], c, s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused X pass (+ optional Z layer)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ psi,
+                                              long long state_stride,
+                                              const double *__restrict__ recs, int rec_stride,
+                                              const PassDesc *__restrict__ d) {
+    using V = typename C2<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *tile = reinterpret_cast<V *>(smem_raw);
+    V *lut = tile + (1 << LT);
+    const int t = threadIdx.x;
+    psi += (long long)blockIdx.y * state_stride;
+    const double *rec = recs + (long long)blockIdx.y * rec_stride;
+
+    const long long tau = blockIdx.x;
+    const int nfixed = d->nfixed;
+    long long base = 0;
+    for (int k = 0; k < nfixed; ++k)
+        if ((tau >> k) & 1) base |= 1ll << d->fixed_pos[k];
+
+    const R c0 = (R)rec[0], s0 = (R)rec[1], c1 = (R)rec[2], s1 = (R)rec[3];
+    const int apply_z = d->apply_z;
+    const int nB1 = d->nB + 1;
+    if (apply_z) {
+        const int nl = (d->nA + 1) * nB1;
+        for (int i = t; i < nl; i += NT) lut[i] = mk<R>((R)rec[4 + 2 * i], (R)rec[5 + 2 * i]);
+    }
+    int lm[LT];
+#pragma unroll
+    for (int j = 0; j < LT; ++j) lm[j] = d->lmap[j];
+
+    V v[NR];
+    // ---- stage 0: global -> registers (lanes along local bits 0..4) ----
+    {
+        long long toff = base;
+#pragma unroll
+        for (int j = 0; j < TB; ++j)
+            if ((t >> j) & 1) toff |= 1ll << lm[j];
+        long long rs[RB];
+#pragma unroll
+        for (int k = 0; k < RB; ++k) rs[k] = 1ll << lm[TB + k];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            long long off = toff;
+#pragma unroll
+            for (int k = 0; k < RB; ++k)
+                if ((r >> k) & 1) off |= rs[k];
+            v[r] = psi[off];
+        }
+        int cls[RB];
+#pragma unroll
+        for (int k = 0; k < RB; ++k) cls[k] = d->reg_cls[0][k];
+        rotate_regs<R>(v, d->rot_mask[0], cls, c0, s0, c1, s1);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) tile[swz(t | (r << TB))] = v[r];
+    }
+    __syncthreads();
+    // ---- stage 1: registers hold local bits 0..3 ----
+    if (d->stage1_on) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = tile[swz(r | (t << RB))];
+        int cls[RB];
+#pragma unroll
+        for (int k = 0; k < RB; ++k) cls[k] = d->reg_cls[1][k];
+        rotate_regs<R>(v, d->rot_mask[1], cls, c0, s0, c1, s1);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) tile[swz(r | (t << RB))] = v[r];
+        __syncthreads();
+    }
+    // ---- stage 2: registers hold local bits 4..7; store to global ----
+    const int tlo = t & 15, thi = t >> 4;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) v[r] = tile[swz(tlo | (r << 4) | (thi << 8))];
+    {
+        int cls[RB];
+#pragma unroll
+        for (int k = 0; k < RB; ++k) cls[k] = d->reg_cls[2][k];
+        rotate_regs<R>(v, d->rot_mask[2], cls, c0, s0, c1, s1);
+    }
+    long long toff = base;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if ((tlo >> j) & 1) toff |= 1ll << lm[j];
+        if ((thi >> j) & 1) toff |= 1ll << lm[8 + j];
+    }
+    long long rs[RB];
+#pragma unroll
+    for (int k = 0; k < RB; ++k) rs[k] = 1ll << lm[4 + k];
+    if (apply_z) {
+        // parity vectors: P(i) = xor of the columns of the set bits of i
+        uint32_t pa = 0, pb = 0;
+        for (int k = 0; k < nfixed; ++k)
+            if ((tau >> k) & 1) { int g = d->fixed_pos[k]; pa ^= d->colA[g]; pb ^= d->colB[g]; }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if ((tlo >> j) & 1) { pa ^= d->colA[lm[j]]; pb ^= d->colB[lm[j]]; }
+            if ((thi >> j) & 1) { pa ^= d->colA[lm[8 + j]]; pb ^= d->colB[lm[8 + j]]; }
+        }
+        uint32_t ra[RB], rb[RB];
+#pragma unroll
+        for (int k = 0; k < RB; ++k) { ra[k] = d->colA[lm[4 + k]]; rb[k] = d->colB[lm[4 + k]]; }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            uint32_t a = pa, b = pb;
+#pragma unroll
+            for (int k = 0; k < RB; ++k)
+                if ((r >> k) & 1) { a ^= ra[k]; b ^= rb[k]; }
+            v[r] = cmul(v[r], lut[__popc(a) * nB1 + __popc(b)]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        long long off = toff;
+#pragma unroll
+        for (int k = 0; k < RB; ++k)
+            if ((r >> k) & 1) off |= rs[k];
+        psi[off] = v[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Parity tables: P(i) = T[0][i & 255] ^ T[1][(i >> 8) & 255] ^ ...
+// ---------------------------------------------------------------------------
+constexpr int MAXBYTES = (MAXQ + 7) / 8;
+
+__device__ __forceinline__ void build_parity_tables(uint2 *tab, const uint32_t *colA,
+                                                    const uint32_t *colB, int n) {
+    const int nbytes = (n + 7) / 8;
+    for (int e = threadIdx.x; e < nbytes * 256; e += blockDim.x) {
+        int k = e >> 8, val = e & 255;
+        uint32_t a = 0, b = 0;
+        for (int j = 0; j < 8; ++j) {
+            int q = 8 * k + j;
+            if (q < n && ((val >> j) & 1)) { a ^= colA[q]; b ^= colB[q]; }
+        }
+        tab[e] = make_uint2(a, b);
+    }
+}
+
+__device__ __forceinline__ uint2 parity_of(const uint2 *tab, long long i, int nbytes) {
+    uint32_t a = 0, b = 0;
+    for (int k = 0; k < nbytes; ++k) {
+        uint2 e = tab[(k << 8) | (int)((i >> (8 * k)) & 255)];
+        a ^= e.x; b ^= e.y;
+    }
+    return make_uint2(a, b);
+}
+
+// Z layer alone, one HBM pass; grid-stride over amplitudes; blockIdx.y = batch.
+template <typename R>
+__global__ void __launch_bounds__(256) k_zdiag(typename C2<R>::T *__restrict__ psi, int n,
+                                               long long state_stride,
+                                               const double *__restrict__ recs, int rec_stride,
+                                               const uint32_t *__restrict__ colA,
+                                               const uint32_t *__restrict__ colB, int nA, int nB) {
+    using V = typename C2<R>::T;
+    __shared__ uint2 tab[MAXBYTES * 256];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *lut = reinterpret_cast<V *>(smem_raw);
+    psi += (long long)blockIdx.y * state_stride;
+    const double *rec = recs + (long long)blockIdx.y * rec_stride;
+    build_parity_tables(tab, colA, colB, n);
+    const int nB1 = nB + 1, nl = (nA + 1) * nB1;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) lut[i] = mk<R>((R)rec[4 + 2 * i], (R)rec[5 + 2 * i]);
+    __syncthreads();
+    const int nbytes = (n + 7) / 8;
+    const long long dim = 1ll << n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dim;
+         i += (long long)gridDim.x * blockDim.x) {
+        uint2 p = parity_of(tab, i, nbytes);
+        psi[i] = cmul(psi[i], lut[__popc(p.x) * nB1 + __popc(p.y)]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Per-gate kernels (one Pauli factor per launch)
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_rx(typename C2<R>::T *__restrict__ psi, int n, long long state_stride, int q,
+                     R c, R s) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= (1ll << (n - 1))) return;
+    psi += (long long)blockIdx.y * state_stride;
+    long long lo = p & ((1ll << q) - 1);
+    long long i0 = ((p >> q) << (q + 1)) | lo;
+    long long i1 = i0 | (1ll << q);
+    auto a = psi[i0], b = psi[i1];
+    xrot(a, b, c, s);
+    psi[i0] = a; psi[i1] = b;
+}
+
+template <typename R>
+__global__ void k_xstring(typename C2<R>::T *__restrict__ psi, int n, long long state_stride,
+                          unsigned long long mask, int top, R c, R s) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= (1ll << (n - 1))) return;
+    psi += (long long)blockIdx.y * state_stride;
+    long long lo = p & ((1ll << top) - 1);
+    long long i0 = ((p >> top) << (top + 1)) | lo;   // bit `top` of i0 is 0
+    long long i1 = i0 ^ (long long)mask;
+    auto a = psi[i0], b = psi[i1];
+    xrot(a, b, c, s);
+    psi[i0] = a; psi[i1] = b;
+}
+
+template <typename R>
+__global__ void k_zterm(typename C2<R>::T *__restrict__ psi, int n, long long state_stride,
+                        unsigned long long mask, R c, R s) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (1ll << n)) return;
+    psi += (long long)blockIdx.y * state_stride;
+    R ss = (__popcll((unsigned long long)i & mask) & 1) ? -s : s;
+    auto a = psi[i];
+    typename C2<R>::T r;
+    r.x = c * a.x - ss * a.y;
+    r.y = c * a.y + ss * a.x;
+    psi[i] = r;
+}
+
+template <typename R>
+__global__ void k_fill(typename C2<R>::T *__restrict__ psi, long long count, R re) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        psi[i] = mk<R>(re, (R)0);
+}
+
+// psi_b <- psi_b / sqrt(norm_b), norm_b = res[b * RED_NV] (device, FP64)
+template <typename R>
+__global__ void k_scale_by_norm(typename C2<R>::T *__restrict__ psi, long long state_stride,
+                                const double *__restrict__ res) {
+    psi += (long long)blockIdx.y * state_stride;
+    const double nrm = res[blockIdx.y * RED_NV];
+    const R f = (R)(1.0 / sqrt(nrm));
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < state_stride;
+         i += (long long)gridDim.x * blockDim.x) {
+        auto a = psi[i];
+        a.x *= f; a.y *= f;
+        psi[i] = a;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions: each block writes RED_NV partials; k_finish sums them in a
+// fixed order (deterministic for a fixed grid).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+template <int NVAL>
+__device__ __forceinline__ void block_store(double (&acc)[NVAL], double *out) {
+    __shared__ double sh[RED_THREADS / 32][RED_NV];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int v = 0; v < NVAL; ++v) {
+        double x = warp_sum(acc[v]);
+        if (l == 0) sh[w][v] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NVAL) {
+        double s = 0.0;
+        for (int k = 0; k < RED_THREADS / 32; ++k) s += sh[k][threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// values: [norm, sum_p <B_p>-weighted count sum (nA - 2 oddA), (nB - 2 oddB), Z-mask]
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_diag(
+    const typename C2<R>::T *__restrict__ psi, int n, long long state_stride,
+    const uint32_t *__restrict__ colA, const uint32_t *__restrict__ colB, int nA, int nB,
+    unsigned long long zmask, double *__restrict__ partials) {
+    __shared__ uint2 tab[MAXBYTES * 256];
+    psi += (long long)blockIdx.y * state_stride;
+    build_parity_tables(tab, colA, colB, n);
+    __syncthreads();
+    const int nbytes = (n + 7) / 8;
+    const long long dim = 1ll << n;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dim;
+         i += (long long)gridDim.x * blockDim.x) {
+        auto a = psi[i];
+        double p = (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+        uint2 par = parity_of(tab, i, nbytes);
+        acc[0] += p;
+        acc[1] += p * (double)(nA - 2 * __popc(par.x));
+        acc[2] += p * (double)(nB - 2 * __popc(par.y));
+        acc[3] += (__popcll((unsigned long long)i & zmask) & 1) ? -p : p;
+    }
+    block_store<4>(acc, partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * RED_NV);
+}
+
+// sum_i conj(a_i) b_{i ^ mask} (re, im); with a == b this is <X_mask>
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_xmask(
+    const typename C2<R>::T *__restrict__ a, const typename C2<R>::T *__restrict__ b, int n,
+    long long state_stride, unsigned long long mask, double *__restrict__ partials) {
+    a += (long long)blockIdx.y * state_stride;
+    b += (long long)blockIdx.y * state_stride;
+    const long long dim = 1ll << n;
+    double acc[2] = {0.0, 0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dim;
+         i += (long long)gridDim.x * blockDim.x) {
+        auto x = a[i];
+        auto y = b[i ^ (long long)mask];
+        acc[0] += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
+        acc[1] += (double)x.x * (double)y.y - (double)x.y * (double)y.x;
+    }
+    block_store<2>(acc, partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * RED_NV);
+}
+
+// res[b * RED_NV + v] = sum over the nblk partials of batch b (fixed order)
+__global__ void k_finish(const double *__restrict__ partials, int nblk, int nval,
+                         double *__restrict__ res) {
+    __shared__ double sh[RED_THREADS];
+    const int b = blockIdx.x;
+    for (int v = 0; v < nval; ++v) {
+        double s = 0.0;
+        for (int k = threadIdx.x; k < nblk; k += blockDim.x)
+            s += partials[((long long)b * nblk + k) * RED_NV + v];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) res[b * RED_NV + v] = sh[0];
+        __syncthreads();
+    }
+}
+
+}  // namespace qsim

@@ -1,0 +1,780 @@
+// qsim.cu -- C ABI (include/qsim.h) over the sm_103a kernels of kernels.cuh.
+//
+// Host side: lattice term tables, the X-pass plan, FP64 operator records
+// (cos/sin of the X angles and the Z-layer phase table per Trotter factor), launch
+// sequencing on the bound stream, and FP64 reductions read back to the host.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qsim.h"
+#include "lattice.h"
+#include "kernels.cuh"
+
+using namespace qsim;
+
+namespace {
+
+thread_local std::string g_create_error;
+constexpr int RED_BLOCKS = 152 * 4;  // reduction grid per batch element (fixed: deterministic)
+constexpr int RES_SLOTS = 160;       // reduction result slots per readback
+
+// One Trotter factor group: exp(-i tau H_X) (angles per X class), then optionally
+// exp(-i dt H_Z) (plaquette and second-class Z angles).
+struct Op {
+    double thx[2];   // X angle per class (sigma^x / tau^x or A_v)
+    double zA, zB;   // Z angles: s*h*dt and s*lambda*dt
+    bool has_z;
+};
+
+struct Coef { double xs, xt, za, zb; };
+
+inline Coef coefficients(const qs_couplings &c, double s) {
+    // -H(s) = sum coef * term, H(s) = (1-s) H0 + s H1
+    return Coef{(1.0 - s) + s * c.g, (1.0 - s) + s * c.J, s * c.h, s * c.lambda};
+}
+
+}  // namespace
+
+struct qs_sim {
+    Lattice lat;
+    int boundary = 0, form = 0, dtype = 0, batch = 1, n = 0;
+    long long dim = 0;
+    void *state[2] = {nullptr, nullptr};
+    size_t state_cap[2] = {0, 0};
+    cudaStream_t stream = nullptr;
+    int method = 0, renorm_every = 0, profile = 0, use_graph = 0;
+    std::string err;
+    // tables
+    int nA = 0, nB = 0, rec_stride = 0;
+    std::vector<PassDesc> passes;          // host copies (apply_z = 0)
+    PassDesc *d_passes = nullptr;          // device: [2 * pass + apply_z]
+    uint32_t *d_colA = nullptr, *d_colB = nullptr;
+    // operator records
+    double *d_rec = nullptr; size_t d_rec_cap = 0;
+    double *h_rec = nullptr; size_t h_rec_cap = 0;
+    cudaEvent_t rec_done = nullptr; bool rec_pending = false;
+    // reductions
+    double *d_partials = nullptr, *d_res = nullptr, *h_res = nullptr;
+    // profiling of the fused pass
+    std::vector<cudaEvent_t> ev_pool; size_t ev_used = 0;
+    long long launches = 0;
+};
+
+#define FAIL(sim, code, ...)                                   \
+    do {                                                       \
+        char _b[512];                                          \
+        snprintf(_b, sizeof(_b), __VA_ARGS__);                 \
+        (sim)->err = _b;                                       \
+        return (code);                                         \
+    } while (0)
+
+#define CK(sim, call)                                                                   \
+    do {                                                                                \
+        cudaError_t _e = (call);                                                        \
+        if (_e != cudaSuccess)                                                          \
+            FAIL(sim, QS_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(_e));           \
+    } while (0)
+
+#define CKL(sim)                                                                         \
+    do {                                                                                 \
+        cudaError_t _e = cudaGetLastError();                                             \
+        if (_e != cudaSuccess) FAIL(sim, QS_ERR_CUDA, "launch: %s", cudaGetErrorString(_e)); \
+    } while (0)
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// pass plan: pass 0 covers global bits 0..11; each further pass keeps a chunk of
+// c >= 4 low bits (>= 128 contiguous bytes) and takes up to 8 new high bits.
+// ---------------------------------------------------------------------------
+void build_passes(qs_sim *s) {
+    const int n = s->n;
+    s->passes.clear();
+    if (n < LT) return;
+    int next = 0;
+    while (next < n) {
+        PassDesc d;
+        memset(&d, 0, sizeof(d));
+        d.n = n;
+        int first = (next == 0);
+        int k = first ? LT : std::min(8, n - next);
+        int c = LT - k;                 // chunk bits (already rotated)
+        bool rot_local[LT];
+        for (int j = 0; j < LT; ++j) {
+            if (j < c) { d.lmap[j] = j; rot_local[j] = first; }
+            else { d.lmap[j] = next + (j - c); rot_local[j] = true; }
+        }
+        if (first) for (int j = 0; j < LT; ++j) { d.lmap[j] = j; rot_local[j] = true; }
+        // stage register bits: stage0 local 8+k, stage1 local k, stage2 local 4+k
+        const int stage_base[3] = {8, 0, 4};
+        for (int st = 0; st < 3; ++st) {
+            unsigned m = 0;
+            for (int kk = 0; kk < RB; ++kk) {
+                int lj = stage_base[st] + kk;
+                if (rot_local[lj]) m |= 1u << kk;
+                d.reg_cls[st][kk] = s->lat.x_class[d.lmap[lj]];
+            }
+            d.rot_mask[st] = m;
+        }
+        d.stage1_on = d.rot_mask[1] != 0;
+        // tile-index bits: every global bit not in lmap, increasing
+        bool used[64] = {false};
+        for (int j = 0; j < LT; ++j) used[d.lmap[j]] = true;
+        int nf = 0;
+        for (int q = 0; q < n; ++q) if (!used[q]) d.fixed_pos[nf++] = q;
+        d.nfixed = nf;
+        d.nA = s->nA; d.nB = s->nB;
+        for (int q = 0; q < n; ++q) {
+            uint32_t a = 0, b = 0;
+            for (size_t p = 0; p < s->lat.plaquettes.size(); ++p)
+                if ((s->lat.plaquettes[p] >> q) & 1) a |= 1u << p;
+            for (size_t p = 0; p < s->lat.second.size(); ++p)
+                if ((s->lat.second[p] >> q) & 1) b |= 1u << p;
+            d.colA[q] = a; d.colB[q] = b;
+        }
+        s->passes.push_back(d);
+        next = first ? LT : next + k;
+    }
+}
+
+void fill_record(const qs_sim *s, const Op &op, double *r) {
+    r[0] = cos(op.thx[0]); r[1] = sin(op.thx[0]);
+    r[2] = cos(op.thx[1]); r[3] = sin(op.thx[1]);
+    if (!op.has_z) return;
+    const int nA = s->nA, nB = s->nB;
+    for (int a = 0; a <= nA; ++a)
+        for (int b = 0; b <= nB; ++b) {
+            // exp(i [zA * sum_p (-1)^{pi_p} + zB * sum_b (-1)^{pi_b}]) with a odd plaquettes, b odd bonds
+            double phi = op.zA * (double)(nA - 2 * a) + op.zB * (double)(nB - 2 * b);
+            r[4 + 2 * (a * (nB + 1) + b)] = cos(phi);
+            r[5 + 2 * (a * (nB + 1) + b)] = sin(phi);
+        }
+}
+
+// ops[k * batch + b]
+std::vector<Op> build_ops(const qs_couplings *c, int batch, const double *sv, double dt,
+                          int n_steps, int order, bool fsal) {
+    std::vector<Op> ops;
+    auto xang = [&](int b, double sk, double tau, double *out) {
+        Coef q = coefficients(c[b], sk);
+        out[0] = q.xs * tau; out[1] = q.xt * tau;
+    };
+    for (int k = 0; k < n_steps; ++k) {
+        if (order == 1) {
+            for (int b = 0; b < batch; ++b) {
+                Op o{}; xang(b, sv[k], dt, o.thx);
+                Coef q = coefficients(c[b], sv[k]);
+                o.zA = q.za * dt; o.zB = q.zb * dt; o.has_z = true;
+                ops.push_back(o);
+            }
+        } else if (fsal) {
+            for (int b = 0; b < batch; ++b) {
+                Op o{};
+                double a[2], p[2] = {0.0, 0.0};
+                xang(b, sv[k], 0.5 * dt, a);
+                if (k > 0) xang(b, sv[k - 1], 0.5 * dt, p);
+                o.thx[0] = a[0] + p[0]; o.thx[1] = a[1] + p[1];
+                Coef q = coefficients(c[b], sv[k]);
+                o.zA = q.za * dt; o.zB = q.zb * dt; o.has_z = true;
+                ops.push_back(o);
+            }
+            if (k == n_steps - 1)
+                for (int b = 0; b < batch; ++b) {
+                    Op o{}; xang(b, sv[k], 0.5 * dt, o.thx); o.has_z = false;
+                    ops.push_back(o);
+                }
+        } else {
+            for (int b = 0; b < batch; ++b) {
+                Op o{}; xang(b, sv[k], 0.5 * dt, o.thx);
+                Coef q = coefficients(c[b], sv[k]);
+                o.zA = q.za * dt; o.zB = q.zb * dt; o.has_z = true;
+                ops.push_back(o);
+            }
+            for (int b = 0; b < batch; ++b) {
+                Op o{}; xang(b, sv[k], 0.5 * dt, o.thx); o.has_z = false;
+                ops.push_back(o);
+            }
+        }
+    }
+    return ops;
+}
+
+template <typename R>
+using V = typename C2<R>::T;
+
+template <typename R>
+qs_status launch_xpass(qs_sim *s, int p, bool apply_z, const double *rec) {
+    const PassDesc &d = s->passes[p];
+    dim3 grid((unsigned)(1ll << d.nfixed), (unsigned)s->batch);
+    size_t smem = (size_t)(1 << LT) * sizeof(V<R>) + (size_t)(s->nA + 1) * (s->nB + 1) * sizeof(V<R>);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (s->profile) {
+        while (s->ev_pool.size() < s->ev_used + 2) {
+            cudaEvent_t e;
+            CK(s, cudaEventCreate(&e));
+            s->ev_pool.push_back(e);
+        }
+        e0 = s->ev_pool[s->ev_used]; e1 = s->ev_pool[s->ev_used + 1];
+        s->ev_used += 2;
+        CK(s, cudaEventRecord(e0, s->stream));
+    }
+    k_xpass<R><<<grid, NT, smem, s->stream>>>((V<R> *)s->state[0], s->dim, rec, s->rec_stride,
+                                               s->d_passes + 2 * p + (apply_z ? 1 : 0));
+    CKL(s);
+    s->launches++;
+    if (s->profile) CK(s, cudaEventRecord(e1, s->stream));
+    return QS_OK;
+}
+
+unsigned grid_for(long long work, int threads) {
+    long long g = (work + threads - 1) / threads;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+template <typename R>
+qs_status launch_zdiag(qs_sim *s, const double *rec) {
+    dim3 grid(152 * 8, (unsigned)s->batch);
+    size_t smem = (size_t)(s->nA + 1) * (s->nB + 1) * sizeof(V<R>);
+    k_zdiag<R><<<grid, 256, smem, s->stream>>>((V<R> *)s->state[0], s->n, s->dim, rec, s->rec_stride,
+                                                s->d_colA, s->d_colB, s->nA, s->nB);
+    CKL(s);
+    s->launches++;
+    return QS_OK;
+}
+
+// Apply ops[first .. first+count) (each a batch of records already on the device at drec).
+template <typename R>
+qs_status run_op_fused(qs_sim *s, const Op *ops_b, const double *drec) {
+    qs_status st;
+    const bool ug = !s->lat.gauge_higgs;
+    const int np = (int)s->passes.size();
+    const bool has_z = ops_b[0].has_z;
+    if (np == 0) {
+        // state smaller than one tile: per-term X factors, then the Z table in one pass
+        for (int b = 0; b < s->batch; ++b) {
+            V<R> *psi = (V<R> *)s->state[0] + (long long)b * s->dim;
+            for (int q = 0; q < s->n; ++q) {
+                double th = ops_b[b].thx[s->lat.x_class[q]];
+                k_rx<R><<<grid_for(s->dim / 2, 256), 256, 0, s->stream>>>(psi, s->n, s->dim, q,
+                                                                            (R)cos(th), (R)sin(th));
+                CKL(s); s->launches++;
+            }
+        }
+    } else {
+        for (int p = 0; p < np; ++p) {
+            bool z_here = has_z && !ug && p == np - 1;
+            if ((st = launch_xpass<R>(s, p, z_here, drec)) != QS_OK) return st;
+        }
+    }
+    if (ug) {
+        for (int b = 0; b < s->batch; ++b) {
+            V<R> *psi = (V<R> *)s->state[0] + (long long)b * s->dim;
+            double th = ops_b[b].thx[1];
+            for (uint64_t m : s->lat.stars) {
+                int top = 63 - __builtin_clzll(m);
+                k_xstring<R><<<grid_for(s->dim / 2, 256), 256, 0, s->stream>>>(
+                    psi, s->n, s->dim, (unsigned long long)m, top, (R)cos(th), (R)sin(th));
+                CKL(s); s->launches++;
+            }
+        }
+    }
+    if (has_z && (ug || np == 0))
+        if ((st = launch_zdiag<R>(s, drec)) != QS_OK) return st;
+    return QS_OK;
+}
+
+// Plain per-gate form: one launch per Pauli factor.
+template <typename R>
+qs_status run_op_pergate(qs_sim *s, const Op *ops_b) {
+    for (int b = 0; b < s->batch; ++b) {
+        const Op &o = ops_b[b];
+        V<R> *psi = (V<R> *)s->state[0] + (long long)b * s->dim;
+        for (int q = 0; q < s->n; ++q) {
+            double th = o.thx[s->lat.x_class[q]];
+            k_rx<R><<<grid_for(s->dim / 2, 256), 256, 0, s->stream>>>(psi, s->n, s->dim, q,
+                                                                        (R)cos(th), (R)sin(th));
+            CKL(s); s->launches++;
+        }
+        if (!s->lat.gauge_higgs) {
+            double th = o.thx[1];
+            for (uint64_t m : s->lat.stars) {
+                int top = 63 - __builtin_clzll(m);
+                k_xstring<R><<<grid_for(s->dim / 2, 256), 256, 0, s->stream>>>(
+                    psi, s->n, s->dim, (unsigned long long)m, top, (R)cos(th), (R)sin(th));
+                CKL(s); s->launches++;
+            }
+        }
+        if (o.has_z) {
+            for (uint64_t m : s->lat.plaquettes) {
+                k_zterm<R><<<grid_for(s->dim, 256), 256, 0, s->stream>>>(
+                    psi, s->n, s->dim, (unsigned long long)m, (R)cos(o.zA), (R)sin(o.zA));
+                CKL(s); s->launches++;
+            }
+            for (uint64_t m : s->lat.second) {
+                k_zterm<R><<<grid_for(s->dim, 256), 256, 0, s->stream>>>(
+                    psi, s->n, s->dim, (unsigned long long)m, (R)cos(o.zB), (R)sin(o.zB));
+                CKL(s); s->launches++;
+            }
+        }
+    }
+    return QS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+template <typename R>
+qs_status reduce_diag(qs_sim *s, const void *state, uint64_t zmask, int slot) {
+    dim3 grid(RED_BLOCKS, (unsigned)s->batch);
+    k_reduce_diag<R><<<grid, RED_THREADS, 0, s->stream>>>((const V<R> *)state, s->n, s->dim, s->d_colA,
+                                                          s->d_colB, s->nA, s->nB,
+                                                          (unsigned long long)zmask, s->d_partials);
+    CKL(s); s->launches++;
+    k_finish<<<s->batch, RED_THREADS, 0, s->stream>>>(s->d_partials, RED_BLOCKS, 4,
+                                                      s->d_res + (size_t)slot * s->batch * RED_NV);
+    CKL(s); s->launches++;
+    return QS_OK;
+}
+
+template <typename R>
+qs_status reduce_xmask(qs_sim *s, const void *a, const void *b, uint64_t mask, int slot) {
+    dim3 grid(RED_BLOCKS, (unsigned)s->batch);
+    k_reduce_xmask<R><<<grid, RED_THREADS, 0, s->stream>>>((const V<R> *)a, (const V<R> *)b, s->n, s->dim,
+                                                           (unsigned long long)mask, s->d_partials);
+    CKL(s); s->launches++;
+    k_finish<<<s->batch, RED_THREADS, 0, s->stream>>>(s->d_partials, RED_BLOCKS, 2,
+                                                      s->d_res + (size_t)slot * s->batch * RED_NV);
+    CKL(s); s->launches++;
+    return QS_OK;
+}
+
+qs_status read_results(qs_sim *s, int slots) {
+    size_t bytes = (size_t)slots * s->batch * RED_NV * sizeof(double);
+    CK(s, cudaMemcpyAsync(s->h_res, s->d_res, bytes, cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    for (size_t i = 0; i < (size_t)slots * s->batch * RED_NV; ++i)
+        if (!std::isfinite(s->h_res[i])) FAIL(s, QS_ERR_NONFINITE, "non-finite reduction result");
+    return QS_OK;
+}
+
+inline double res(const qs_sim *s, int slot, int b, int v) {
+    return s->h_res[((size_t)slot * s->batch + b) * RED_NV + v];
+}
+
+template <typename R>
+qs_status renormalise(qs_sim *s) {
+    qs_status st;
+    if ((st = reduce_diag<R>(s, s->state[0], 0, 0)) != QS_OK) return st;
+    dim3 grid(152 * 8, (unsigned)s->batch);
+    k_scale_by_norm<R><<<grid, 256, 0, s->stream>>>((V<R> *)s->state[0], s->dim, s->d_res);
+    CKL(s); s->launches++;
+    return QS_OK;
+}
+
+qs_status upload_records(qs_sim *s, const std::vector<Op> &ops) {
+    size_t need = ops.size() * (size_t)s->rec_stride;
+    if (s->rec_pending) {
+        CK(s, cudaEventSynchronize(s->rec_done));
+        s->rec_pending = false;
+    }
+    if (need > s->h_rec_cap) {
+        if (s->h_rec) cudaFreeHost(s->h_rec);
+        s->h_rec = nullptr;
+        if (cudaMallocHost((void **)&s->h_rec, need * sizeof(double)) != cudaSuccess)
+            FAIL(s, QS_ERR_OOM, "pinned record buffer (%zu doubles)", need);
+        s->h_rec_cap = need;
+    }
+    if (need > s->d_rec_cap) {
+        // the previous device buffer may still be read by queued kernels
+        if (s->d_rec) { CK(s, cudaStreamSynchronize(s->stream)); cudaFree(s->d_rec); }
+        s->d_rec = nullptr;
+        if (cudaMalloc((void **)&s->d_rec, need * sizeof(double)) != cudaSuccess)
+            FAIL(s, QS_ERR_OOM, "device record buffer (%zu doubles)", need);
+        s->d_rec_cap = need;
+    } else {
+        // kernels queued earlier may still read d_rec: order the copy after them
+    }
+    memset(s->h_rec, 0, need * sizeof(double));
+    for (size_t i = 0; i < ops.size(); ++i) fill_record(s, ops[i], s->h_rec + i * s->rec_stride);
+    CK(s, cudaMemcpyAsync(s->d_rec, s->h_rec, need * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaEventRecord(s->rec_done, s->stream));
+    s->rec_pending = true;
+    return QS_OK;
+}
+
+template <typename R>
+qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit) {
+    qs_status st;
+    const int B = s->batch;
+    const size_t nops = ops.size() / B;
+    if (s->method == 0) {
+        if ((st = upload_records(s, ops)) != QS_OK) return st;
+        for (size_t k = 0; k < nops; ++k) {
+            if ((st = run_op_fused<R>(s, &ops[k * B], s->d_rec + k * B * (size_t)s->rec_stride)) != QS_OK)
+                return st;
+            if (s->renorm_every > 0 && steps_per_renorm_unit > 0 &&
+                ((k + 1) % ((size_t)s->renorm_every * steps_per_renorm_unit) == 0 || k + 1 == nops))
+                if ((st = renormalise<R>(s)) != QS_OK) return st;
+        }
+    } else {
+        for (size_t k = 0; k < nops; ++k) {
+            if ((st = run_op_pergate<R>(s, &ops[k * B])) != QS_OK) return st;
+            if (s->renorm_every > 0 && steps_per_renorm_unit > 0 &&
+                ((k + 1) % ((size_t)s->renorm_every * steps_per_renorm_unit) == 0 || k + 1 == nops))
+                if ((st = renormalise<R>(s)) != QS_OK) return st;
+        }
+    }
+    return QS_OK;
+}
+
+qs_status check_ready(qs_sim *s) {
+    if (!s) return QS_ERR_ARG;
+    if (!s->state[0]) FAIL(s, QS_ERR_STATE, "no state bound (qs_bind_state slot 0)");
+    return QS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch, qs_sim **out) {
+    g_create_error.clear();
+    if (!out) { g_create_error = "out is NULL"; return QS_ERR_ARG; }
+    *out = nullptr;
+    if (boundary != QS_PERIODIC && boundary != QS_OPEN) { g_create_error = "bad boundary"; return QS_ERR_ARG; }
+    if (form != QS_GAUGE_HIGGS && form != QS_UNITARY_GAUGE) { g_create_error = "bad form"; return QS_ERR_ARG; }
+    if (dtype != QS_C64 && dtype != QS_C128) { g_create_error = "bad dtype"; return QS_ERR_ARG; }
+    if (batch < 1 || batch > 65535) { g_create_error = "batch must be in [1, 65535]"; return QS_ERR_ARG; }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        g_create_error = "no CUDA device";
+        return QS_ERR_CUDA;
+    }
+    qs_sim *s = new (std::nothrow) qs_sim();
+    if (!s) { g_create_error = "host allocation failed"; return QS_ERR_OOM; }
+    try {
+        s->lat = make_lattice(Lx, Ly, boundary == QS_PERIODIC, form == QS_GAUGE_HIGGS);
+    } catch (const std::exception &e) {
+        g_create_error = e.what();
+        delete s;
+        return QS_ERR_ARG;
+    }
+    s->boundary = boundary; s->form = form; s->dtype = dtype; s->batch = batch;
+    s->n = s->lat.n_qubits;
+    if (s->n > 34 || s->n < 2) {
+        g_create_error = "qubit count must be in [2, 34]";
+        delete s;
+        return QS_ERR_ARG;
+    }
+    s->dim = 1ll << s->n;
+    s->nA = (int)s->lat.plaquettes.size();
+    s->nB = (int)s->lat.second.size();
+    if (s->nA > 32 || s->nB > 32) { g_create_error = "more than 32 terms in a Z class"; delete s; return QS_ERR_ARG; }
+    s->rec_stride = record_doubles(s->nA, s->nB);
+    build_passes(s);
+    auto fail = [&](const char *what) {
+        g_create_error = what;
+        qs_destroy(s);
+        return QS_ERR_OOM;
+    };
+    std::vector<PassDesc> dev;
+    for (auto &d : s->passes) {
+        PassDesc a = d; a.apply_z = 0; dev.push_back(a);
+        PassDesc b = d; b.apply_z = 1; dev.push_back(b);
+    }
+    if (!dev.empty()) {
+        if (cudaMalloc((void **)&s->d_passes, dev.size() * sizeof(PassDesc)) != cudaSuccess) return fail("pass table");
+        if (cudaMemcpy(s->d_passes, dev.data(), dev.size() * sizeof(PassDesc), cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail("pass table copy");
+    }
+    std::vector<uint32_t> ca(MAXQ, 0), cb(MAXQ, 0);
+    for (int q = 0; q < s->n; ++q) {
+        for (int p = 0; p < s->nA; ++p) if ((s->lat.plaquettes[p] >> q) & 1) ca[q] |= 1u << p;
+        for (int p = 0; p < s->nB; ++p) if ((s->lat.second[p] >> q) & 1) cb[q] |= 1u << p;
+    }
+    if (cudaMalloc((void **)&s->d_colA, MAXQ * sizeof(uint32_t)) != cudaSuccess) return fail("columns");
+    if (cudaMalloc((void **)&s->d_colB, MAXQ * sizeof(uint32_t)) != cudaSuccess) return fail("columns");
+    if (cudaMemcpy(s->d_colA, ca.data(), MAXQ * 4, cudaMemcpyHostToDevice) != cudaSuccess) return fail("columns copy");
+    if (cudaMemcpy(s->d_colB, cb.data(), MAXQ * 4, cudaMemcpyHostToDevice) != cudaSuccess) return fail("columns copy");
+    size_t pbytes = (size_t)RED_BLOCKS * batch * RED_NV * sizeof(double);
+    size_t rbytes = (size_t)RES_SLOTS * batch * RED_NV * sizeof(double);
+    if (cudaMalloc((void **)&s->d_partials, pbytes) != cudaSuccess) return fail("partials");
+    if (cudaMalloc((void **)&s->d_res, rbytes) != cudaSuccess) return fail("results");
+    if (cudaMallocHost((void **)&s->h_res, rbytes) != cudaSuccess) return fail("pinned results");
+    if (cudaEventCreateWithFlags(&s->rec_done, cudaEventDisableTiming) != cudaSuccess) return fail("event");
+    size_t smem64 = (size_t)(1 << LT) * 16 + (size_t)(s->nA + 1) * (s->nB + 1) * 16;
+    cudaFuncSetAttribute(k_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
+    cudaFuncSetAttribute(k_xpass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
+    *out = s;
+    return QS_OK;
+}
+
+void qs_destroy(qs_sim *s) {
+    if (!s) return;
+    if (s->stream || true) cudaStreamSynchronize(s->stream);
+    cudaFree(s->d_passes);
+    cudaFree(s->d_colA);
+    cudaFree(s->d_colB);
+    cudaFree(s->d_rec);
+    cudaFree(s->d_partials);
+    cudaFree(s->d_res);
+    if (s->h_rec) cudaFreeHost(s->h_rec);
+    if (s->h_res) cudaFreeHost(s->h_res);
+    if (s->rec_done) cudaEventDestroy(s->rec_done);
+    for (auto e : s->ev_pool) cudaEventDestroy(e);
+    delete s;
+}
+
+const char *qs_last_error(const qs_sim *s) {
+    return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+int qs_num_qubits(const qs_sim *s) { return s ? s->n : -1; }
+
+size_t qs_state_bytes(const qs_sim *s) {
+    if (!s) return 0;
+    return (size_t)s->batch * (size_t)s->dim * (s->dtype == QS_C64 ? 8u : 16u);
+}
+
+qs_status qs_bind_state(qs_sim *s, int slot, void *ptr, size_t bytes) {
+    if (!s) return QS_ERR_ARG;
+    if (slot < 0 || slot > 1) FAIL(s, QS_ERR_ARG, "slot must be 0 or 1");
+    if (!ptr) FAIL(s, QS_ERR_ARG, "null device pointer");
+    if (((uintptr_t)ptr & 255u) != 0) FAIL(s, QS_ERR_ARG, "state pointer must be 256-byte aligned");
+    if (bytes < qs_state_bytes(s)) FAIL(s, QS_ERR_ARG, "buffer of %zu bytes < %zu", bytes, qs_state_bytes(s));
+    s->state[slot] = ptr;
+    s->state_cap[slot] = bytes;
+    return QS_OK;
+}
+
+qs_status qs_set_stream(qs_sim *s, void *stream) {
+    if (!s) return QS_ERR_ARG;
+    s->stream = (cudaStream_t)stream;
+    return QS_OK;
+}
+
+qs_status qs_set_option(qs_sim *s, int key, long long value) {
+    if (!s) return QS_ERR_ARG;
+    switch (key) {
+        case QS_OPT_METHOD:
+            if (value != 0 && value != 1) FAIL(s, QS_ERR_ARG, "method must be 0 or 1");
+            s->method = (int)value; return QS_OK;
+        case QS_OPT_RENORM_EVERY:
+            if (value < 0) FAIL(s, QS_ERR_ARG, "renorm interval must be >= 0");
+            s->renorm_every = (int)value; return QS_OK;
+        case QS_OPT_PROFILE: s->profile = value != 0; return QS_OK;
+        case QS_OPT_GRAPH: s->use_graph = value != 0; return QS_OK;
+        default: FAIL(s, QS_ERR_ARG, "unknown option %d", key);
+    }
+}
+
+qs_status qs_init_plus(qs_sim *s) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    long long count = s->dim * s->batch;
+    double a = 1.0 / sqrt((double)s->dim);
+    if (s->dtype == QS_C64)
+        k_fill<float><<<152 * 8, 256, 0, s->stream>>>((float2 *)s->state[0], count, (float)a);
+    else
+        k_fill<double><<<152 * 8, 256, 0, s->stream>>>((double2 *)s->state[0], count, a);
+    CKL(s); s->launches++;
+    return QS_OK;
+}
+
+qs_status qs_upload_state(qs_sim *s, const void *host, size_t bytes) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (!host || bytes != qs_state_bytes(s)) FAIL(s, QS_ERR_ARG, "host buffer must hold qs_state_bytes");
+    CK(s, cudaMemcpyAsync(s->state[0], host, bytes, cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    return QS_OK;
+}
+
+qs_status qs_download_state(qs_sim *s, void *host, size_t bytes) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (!host || bytes != qs_state_bytes(s)) FAIL(s, QS_ERR_ARG, "host buffer must hold qs_state_bytes");
+    CK(s, cudaMemcpyAsync(host, s->state[0], bytes, cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    return QS_OK;
+}
+
+static qs_status evolve_impl(qs_sim *s, const qs_couplings *c, const double *sv, double dt, int n_steps,
+                             int order) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (!c || !sv) FAIL(s, QS_ERR_ARG, "null couplings or schedule");
+    if (order != 1 && order != 2) FAIL(s, QS_ERR_ARG, "order must be 1 or 2");
+    if (n_steps < 0) FAIL(s, QS_ERR_ARG, "n_steps < 0");
+    if (!std::isfinite(dt)) FAIL(s, QS_ERR_ARG, "dt not finite");
+    if (n_steps == 0) return QS_OK;
+    bool fsal = (s->method == 0);
+    std::vector<Op> ops = build_ops(c, s->batch, sv, dt, n_steps, order, fsal);
+    int per_step = (order == 2 && !fsal) ? 2 : 1;
+    if (s->dtype == QS_C64) return run_ops<float>(s, ops, per_step);
+    return run_ops<double>(s, ops, per_step);
+}
+
+qs_status qs_trotter_step(qs_sim *s, const qs_couplings *c, double sv, double dt, int order) {
+    return evolve_impl(s, c, &sv, dt, 1, order);
+}
+
+qs_status qs_evolve(qs_sim *s, const qs_couplings *c, const double *sv, double dt, int n_steps, int order) {
+    return evolve_impl(s, c, sv, dt, n_steps, order);
+}
+
+}  // extern "C"
+
+template <typename R>
+static qs_status expect_impl(qs_sim *s, int kind, int index, const qs_couplings *c, double sval, double *out) {
+    qs_status st;
+    const Lattice &L = s->lat;
+    const int B = s->batch;
+    auto xm = [&](uint64_t m, int slot) { return reduce_xmask<R>(s, s->state[0], s->state[0], m, slot); };
+    switch (kind) {
+        case QS_NORM:
+            if ((st = reduce_diag<R>(s, s->state[0], 0, 0)) != QS_OK) return st;
+            if ((st = read_results(s, 1)) != QS_OK) return st;
+            for (int b = 0; b < B; ++b) out[b] = res(s, 0, b, 0);
+            return QS_OK;
+        case QS_PLAQUETTE:
+        case QS_WILSON: {
+            uint64_t m = 0;
+            if (kind == QS_PLAQUETTE) {
+                if (index < -1 || index >= (int)L.plaquettes.size()) FAIL(s, QS_ERR_ARG, "plaquette index");
+                if (index >= 0) m = L.plaquettes[index];
+            } else {
+                if (index < 0 || index >= (int)L.wilson.size()) FAIL(s, QS_ERR_ARG, "Wilson loop index");
+                m = L.wilson[index];
+            }
+            if ((st = reduce_diag<R>(s, s->state[0], m, 0)) != QS_OK) return st;
+            if ((st = read_results(s, 1)) != QS_OK) return st;
+            for (int b = 0; b < B; ++b)
+                out[b] = (kind == QS_PLAQUETTE && index == -1) ? res(s, 0, b, 1) / L.plaquettes.size()
+                                                               : res(s, 0, b, 3);
+            return QS_OK;
+        }
+        case QS_X:
+        case QS_GAUSS:
+        case QS_THOOFT: {
+            uint64_t m;
+            if (kind == QS_X) {
+                if (index < 0 || index >= s->n) FAIL(s, QS_ERR_ARG, "qubit index");
+                m = 1ull << index;
+            } else if (kind == QS_GAUSS) {
+                if (index < 0 || index >= (int)L.gauss.size()) FAIL(s, QS_ERR_ARG, "Gauss index (gauge-Higgs form only)");
+                m = L.gauss[index];
+            } else {
+                if (index < 0 || index >= (int)L.thooft.size()) FAIL(s, QS_ERR_ARG, "'t Hooft index");
+                m = L.thooft[index];
+            }
+            if ((st = xm(m, 0)) != QS_OK) return st;
+            if ((st = read_results(s, 1)) != QS_OK) return st;
+            for (int b = 0; b < B; ++b) out[b] = res(s, 0, b, 0);
+            return QS_OK;
+        }
+        case QS_ENERGY:
+        case QS_ENERGY_S: {
+            if (!c) FAIL(s, QS_ERR_ARG, "energy needs couplings");
+            double sv = (kind == QS_ENERGY) ? 1.0 : sval;
+            int slot = 0;
+            if ((st = reduce_diag<R>(s, s->state[0], 0, slot++)) != QS_OK) return st;
+            for (int q = 0; q < s->n; ++q)
+                if ((st = xm(1ull << q, slot++)) != QS_OK) return st;
+            int star0 = slot;
+            if (!L.gauge_higgs)
+                for (uint64_t m : L.stars)
+                    if ((st = xm(m, slot++)) != QS_OK) return st;
+            if ((st = read_results(s, slot)) != QS_OK) return st;
+            for (int b = 0; b < B; ++b) {
+                Coef q = coefficients(c[b], sv);
+                double e = -q.za * res(s, 0, b, 1) - q.zb * res(s, 0, b, 2);
+                for (int k = 0; k < s->n; ++k)
+                    e -= (L.x_class[k] ? q.xt : q.xs) * res(s, 1 + k, b, 0);
+                for (int k = star0; k < slot; ++k) e -= q.xt * res(s, k, b, 0);
+                out[b] = e;
+            }
+            return QS_OK;
+        }
+        default:
+            FAIL(s, QS_ERR_ARG, "unknown observable %d", kind);
+    }
+}
+
+extern "C" {
+
+qs_status qs_expect(qs_sim *s, int kind, int index, const qs_couplings *c, double sval, double *out) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (!out) FAIL(s, QS_ERR_ARG, "null output");
+    if (s->dtype == QS_C64) return expect_impl<float>(s, kind, index, c, sval, out);
+    return expect_impl<double>(s, kind, index, c, sval, out);
+}
+
+qs_status qs_expect_pauli(qs_sim *s, int type, uint64_t mask, double *out) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (!out) FAIL(s, QS_ERR_ARG, "null output");
+    if (type != 0 && type != 1) FAIL(s, QS_ERR_ARG, "type must be 0 (Z) or 1 (X)");
+    if (s->n < 64 && (mask >> s->n) != 0) FAIL(s, QS_ERR_ARG, "mask has bits beyond the qubit count");
+    if (type == 0) {
+        st = s->dtype == QS_C64 ? reduce_diag<float>(s, s->state[0], mask, 0)
+                                : reduce_diag<double>(s, s->state[0], mask, 0);
+    } else {
+        st = s->dtype == QS_C64 ? reduce_xmask<float>(s, s->state[0], s->state[0], mask, 0)
+                                : reduce_xmask<double>(s, s->state[0], s->state[0], mask, 0);
+    }
+    if (st != QS_OK) return st;
+    if ((st = read_results(s, 1)) != QS_OK) return st;
+    for (int b = 0; b < s->batch; ++b) out[b] = res(s, 0, b, type == 0 ? 3 : 0);
+    return QS_OK;
+}
+
+qs_status qs_fidelity(qs_sim *s, const void *ref, double *out) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (!ref || !out) FAIL(s, QS_ERR_ARG, "null argument");
+    st = s->dtype == QS_C64 ? reduce_xmask<float>(s, ref, s->state[0], 0, 0)
+                            : reduce_xmask<double>(s, ref, s->state[0], 0, 0);
+    if (st != QS_OK) return st;
+    if ((st = read_results(s, 1)) != QS_OK) return st;
+    for (int b = 0; b < s->batch; ++b) {
+        double re = res(s, 0, b, 0), im = res(s, 0, b, 1);
+        out[b] = re * re + im * im;
+    }
+    return QS_OK;
+}
+
+qs_status qs_profile_read(qs_sim *s, double *total_ms, long long *count) {
+    if (!s || !total_ms || !count) return QS_ERR_ARG;
+    CK(s, cudaStreamSynchronize(s->stream));
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
+        float ms = 0.f;
+        CK(s, cudaEventElapsedTime(&ms, s->ev_pool[i], s->ev_pool[i + 1]));
+        tot += ms;
+    }
+    *total_ms = tot;
+    *count = (long long)(s->ev_used / 2);
+    s->ev_used = 0;
+    return QS_OK;
+}
+
+long long qs_launch_count(qs_sim *s) {
+    if (!s) return -1;
+    long long v = s->launches;
+    s->launches = 0;
+    return v;
+}
+
+}  // extern "C"

@@ -1,0 +1,304 @@
+"""Python binding of the C ABI in include/qsim.h (argument marshalling only).
+
+Every step of the evolution, every observable and every reduction runs in the
+CUDA kernels of libqsim.so; this module only converts arguments, owns the
+borrowed state tensors (allocated by PyTorch on the GPU) and raises on error.
+There is no CPU path: if the library cannot be loaded or built, import fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+
+from . import build as _build
+
+QS_OK = 0
+STATUS = {0: "QS_OK", 1: "QS_ERR_ARG", 2: "QS_ERR_OOM", 3: "QS_ERR_CUDA", 4: "QS_ERR_NONFINITE",
+          5: "QS_ERR_TIMEOUT", 6: "QS_ERR_STATE"}
+QS_PERIODIC, QS_OPEN = 0, 1
+QS_GAUGE_HIGGS, QS_UNITARY_GAUGE = 0, 1
+QS_C64, QS_C128 = 0, 1
+QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
+QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH = range(4)
+
+
+class QsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class qs_couplings(ctypes.Structure):
+    _fields_ = [("J", ctypes.c_double), ("h", ctypes.c_double), ("g", ctypes.c_double),
+                ("lambda_", ctypes.c_double)]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+_LL = ctypes.c_longlong
+_U64 = ctypes.c_uint64
+_CP = ctypes.POINTER(qs_couplings)
+_DP = ctypes.POINTER(ctypes.c_double)
+
+_SIGS = {
+    "qs_create": ([_I, _I, _I, _I, _I, _I, ctypes.POINTER(_P)], _I),
+    "qs_destroy": ([_P], None),
+    "qs_last_error": ([_P], ctypes.c_char_p),
+    "qs_num_qubits": ([_P], _I),
+    "qs_state_bytes": ([_P], _SZ),
+    "qs_bind_state": ([_P, _I, _P, _SZ], _I),
+    "qs_set_stream": ([_P, _P], _I),
+    "qs_set_option": ([_P, _I, _LL], _I),
+    "qs_init_plus": ([_P], _I),
+    "qs_upload_state": ([_P, _P, _SZ], _I),
+    "qs_download_state": ([_P, _P, _SZ], _I),
+    "qs_trotter_step": ([_P, _CP, _D, _D, _I], _I),
+    "qs_evolve": ([_P, _CP, _DP, _D, _I, _I], _I),
+    "qs_expect": ([_P, _I, _I, _CP, _D, _DP], _I),
+    "qs_expect_pauli": ([_P, _I, _U64, _DP], _I),
+    "qs_fidelity": ([_P, _P, _DP], _I),
+    "qs_profile_read": ([_P, _DP, ctypes.POINTER(_LL)], _I),
+    "qs_launch_count": ([_P], _LL),
+}
+
+
+def library() -> ctypes.CDLL:
+    """Load libqsim.so (building it with nvcc first if it is missing or stale)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _LIB = lib
+    return _LIB
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(sim, status: int):
+    if status != QS_OK:
+        msg = library().qs_last_error(sim)
+        raise QsError(status, msg.decode() if msg else "")
+
+
+def _couplings(cs, batch: int):
+    arr = (qs_couplings * batch)()
+    if isinstance(cs, (tuple, list)) and len(cs) and not isinstance(cs[0], (tuple, list, dict, qs_couplings)):
+        cs = [cs]
+    cs = list(cs)
+    if len(cs) == 1 and batch > 1:
+        cs = cs * batch
+    if len(cs) != batch:
+        raise ValueError(f"need {batch} coupling records, got {len(cs)}")
+    for i, c in enumerate(cs):
+        if isinstance(c, qs_couplings):
+            arr[i] = c
+        elif isinstance(c, dict):
+            arr[i] = qs_couplings(c.get("J", 1.0), c.get("h", 1.0), c["g"], c["lambda"])
+        else:   # (g, lambda[, J, h])
+            g, lam = c[0], c[1]
+            J = c[2] if len(c) > 2 else 1.0
+            h = c[3] if len(c) > 3 else 1.0
+            arr[i] = qs_couplings(J, h, g, lam)
+    return arr
+
+
+# ---------------------------------------------------------------------------
+# thin wrappers with the C names
+# ---------------------------------------------------------------------------
+def qs_create(Lx, Ly, boundary=QS_PERIODIC, form=QS_GAUGE_HIGGS, dtype=QS_C64, batch=1):
+    h = _P()
+    st = library().qs_create(Lx, Ly, boundary, form, dtype, batch, ctypes.byref(h))
+    _check(None, st)
+    return h
+
+
+def qs_destroy(sim):
+    library().qs_destroy(sim)
+
+
+def qs_last_error(sim=None) -> str:
+    msg = library().qs_last_error(sim)
+    return msg.decode() if msg else ""
+
+
+def qs_num_qubits(sim) -> int:
+    return library().qs_num_qubits(sim)
+
+
+def qs_state_bytes(sim) -> int:
+    return library().qs_state_bytes(sim)
+
+
+def qs_bind_state(sim, slot: int, dev_ptr: int, nbytes: int):
+    _check(sim, library().qs_bind_state(sim, slot, dev_ptr, nbytes))
+
+
+def qs_set_stream(sim, stream_handle: int):
+    _check(sim, library().qs_set_stream(sim, stream_handle))
+
+
+def qs_set_option(sim, key: int, value: int):
+    _check(sim, library().qs_set_option(sim, key, int(value)))
+
+
+def qs_init_plus(sim):
+    _check(sim, library().qs_init_plus(sim))
+
+
+def qs_upload_state(sim, host_ptr: int, nbytes: int):
+    _check(sim, library().qs_upload_state(sim, host_ptr, nbytes))
+
+
+def qs_download_state(sim, host_ptr: int, nbytes: int):
+    _check(sim, library().qs_download_state(sim, host_ptr, nbytes))
+
+
+def qs_trotter_step(sim, couplings, s: float, dt: float, order: int, batch: int = 1):
+    arr = _couplings(couplings, batch)
+    _check(sim, library().qs_trotter_step(sim, arr, s, dt, order))
+
+
+def qs_evolve(sim, couplings, s: Sequence[float], dt: float, order: int, batch: int = 1):
+    arr = _couplings(couplings, batch)
+    sv = np.ascontiguousarray(s, dtype=np.float64)
+    _check(sim, library().qs_evolve(sim, arr, sv.ctypes.data_as(_DP), dt, int(sv.size), order))
+
+
+def qs_expect(sim, kind: int, index: int = 0, couplings=None, s: float = 1.0, batch: int = 1):
+    out = np.zeros(batch, dtype=np.float64)
+    arr = _couplings(couplings, batch) if couplings is not None else None
+    _check(sim, library().qs_expect(sim, kind, index, arr, s, out.ctypes.data_as(_DP)))
+    return out
+
+
+def qs_expect_pauli(sim, ptype: int, mask: int, batch: int = 1):
+    out = np.zeros(batch, dtype=np.float64)
+    _check(sim, library().qs_expect_pauli(sim, ptype, mask, out.ctypes.data_as(_DP)))
+    return out
+
+
+def qs_fidelity(sim, ref_dev_ptr: int, batch: int = 1):
+    out = np.zeros(batch, dtype=np.float64)
+    _check(sim, library().qs_fidelity(sim, ref_dev_ptr, out.ctypes.data_as(_DP)))
+    return out
+
+
+def qs_profile_read(sim):
+    ms = ctypes.c_double()
+    cnt = _LL()
+    _check(sim, library().qs_profile_read(sim, ctypes.byref(ms), ctypes.byref(cnt)))
+    return ms.value, cnt.value
+
+
+def qs_launch_count(sim) -> int:
+    return library().qs_launch_count(sim)
+
+
+# ---------------------------------------------------------------------------
+# convenience object: owns a torch state buffer on the GPU and a qs_sim handle
+# ---------------------------------------------------------------------------
+class Simulator:
+    """Lattice simulator with PyTorch-allocated device state(s).
+
+    form: "gh" (gauge-Higgs, Eq. (1)) or "ug" (unitary gauge, Eq. (4));
+    dtype: "c64" or "c128"; boundary: "periodic" or "open".
+    """
+
+    def __init__(self, Lx: int, Ly: int, form: str = "gh", dtype: str = "c64",
+                 boundary: str = "periodic", batch: int = 1, device: str = "cuda:0",
+                 method: str = "fused", renorm_every: int = 0, aux: bool = False):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("the qsim engine needs a CUDA GPU; there is no CPU path")
+        self.torch = torch
+        self.batch = batch
+        self.form = form
+        self.dtype_name = dtype
+        self.device = torch.device(device)
+        torch.cuda.set_device(self.device)
+        self.h = qs_create(Lx, Ly, QS_PERIODIC if boundary == "periodic" else QS_OPEN,
+                           QS_GAUGE_HIGGS if form == "gh" else QS_UNITARY_GAUGE,
+                           QS_C64 if dtype == "c64" else QS_C128, batch)
+        self.n = qs_num_qubits(self.h)
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        self.state = torch.empty((batch, 1 << self.n), dtype=tdt, device=self.device)
+        qs_bind_state(self.h, 0, self.state.data_ptr(), self.state.numel() * self.state.element_size())
+        self.aux = None
+        if aux:
+            self.aux = torch.empty_like(self.state)
+            qs_bind_state(self.h, 1, self.aux.data_ptr(), self.aux.numel() * self.aux.element_size())
+        self.set_stream(torch.cuda.current_stream(self.device))
+        self.set_option(QS_OPT_METHOD, 0 if method == "fused" else 1)
+        self.set_option(QS_OPT_RENORM_EVERY, renorm_every)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            qs_destroy(h)
+            self.h = None
+
+    # --- plumbing ---
+    def set_stream(self, stream):
+        self.stream = stream
+        qs_set_stream(self.h, stream.cuda_stream)
+
+    def set_option(self, key, value):
+        qs_set_option(self.h, key, value)
+
+    @property
+    def state_bytes(self) -> int:
+        return qs_state_bytes(self.h)
+
+    # --- evolution ---
+    def init_plus(self):
+        qs_init_plus(self.h)
+
+    def trotter_step(self, couplings, s, dt, order=2):
+        qs_trotter_step(self.h, couplings, s, dt, order, self.batch)
+
+    def evolve(self, couplings, s, dt, order=2):
+        qs_evolve(self.h, couplings, s, dt, order, self.batch)
+
+    # --- observables ---
+    def expect(self, kind, index=0, couplings=None, s=1.0):
+        return qs_expect(self.h, kind, index, couplings, s, self.batch)
+
+    def energy(self, couplings, s=None):
+        if s is None:
+            return self.expect(QS_ENERGY, 0, couplings, 1.0)
+        return self.expect(QS_ENERGY_S, 0, couplings, s)
+
+    def expect_pauli(self, ptype, mask):
+        return qs_expect_pauli(self.h, ptype, mask, self.batch)
+
+    def fidelity(self, ref_state):
+        assert ref_state.shape == self.state.shape and ref_state.dtype == self.state.dtype
+        return qs_fidelity(self.h, ref_state.data_ptr(), self.batch)
+
+    def upload(self, host_tensor):
+        assert host_tensor.is_contiguous() and host_tensor.numel() == self.state.numel()
+        qs_upload_state(self.h, host_tensor.data_ptr(), self.state_bytes)
+
+    def download(self, host_tensor=None):
+        if host_tensor is None:
+            host_tensor = self.torch.empty(self.state.shape, dtype=self.state.dtype, pin_memory=True)
+        qs_download_state(self.h, host_tensor.data_ptr(), self.state_bytes)
+        return host_tensor
+
+    def profile_read(self):
+        return qs_profile_read(self.h)
+
+    def launch_count(self):
+        return qs_launch_count(self.h)
