@@ -45,8 +45,9 @@ struct PassDesc {
     uint32_t colB[MAXQ];        // per global qubit: bonds / sigma^z terms containing it
 };
 
-// Operator record (doubles): [cos_sigma, sin_sigma, cos_tau, sin_tau,
-//   then (nA+1)(nB+1) complex phases exp(i phi(nA_odd, nB_odd)) as (re, im)].
+// Operator record (doubles): [u_sigma, s_sigma, u_tau, s_tau, then (nA+1)(nB+1)
+//   phase pairs (u, s) of exp(i phi(nA_odd, nB_odd))], where exp(i t) = (1 - u) + i s,
+//   u = 1 - cos t, s = sin t (u keeps full relative precision for small angles).
 __host__ __device__ inline int record_doubles(int nA, int nB) {
     int r = 4 + 2 * (nA + 1) * (nB + 1);
     return (r + 1) & ~1;
@@ -61,32 +62,37 @@ __device__ __forceinline__ typename C2<R>::T mk(R x, R y) {
     typename C2<R>::T v; v.x = x; v.y = y; return v;
 }
 
-// (a, b) <- exp(i theta X) (a, b):  a' = c a + i s b,  b' = i s a + c b
+// (a, b) <- exp(i theta X) (a, b) with cos theta = 1 - u, sin theta = s:
+//   a' = a - u a + i s b,  b' = b - u b + i s a
 template <typename V, typename R>
-__device__ __forceinline__ void xrot(V &a, V &b, R c, R s) {
+__device__ __forceinline__ void xrot(V &a, V &b, R u, R s) {
     R ar = a.x, ai = a.y, br = b.x, bi = b.y;
-    a.x = c * ar - s * bi; a.y = c * ai + s * br;
-    b.x = c * br - s * ai; b.y = c * bi + s * ar;
+    a.x = fma(-s, bi, fma(-u, ar, ar)); a.y = fma(s, br, fma(-u, ai, ai));
+    b.x = fma(-s, ai, fma(-u, br, br)); b.y = fma(s, ar, fma(-u, bi, bi));
 }
 
+// v * exp(i t) with exp(i t) = (1 - p.x) + i p.y
 template <typename V>
-__device__ __forceinline__ V cmul(V a, V b) {
-    V r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+__device__ __forceinline__ V cphase(V v, V p) {
+    V r;
+    r.x = fma(-p.y, v.y, fma(-p.x, v.x, v.x));
+    r.y = fma(p.y, v.x, fma(-p.x, v.y, v.y));
+    return r;
 }
 
 __device__ __forceinline__ int swz(int l) { return l ^ ((l >> 4) & 15); }
 
 template <typename R, typename V>
 __device__ __forceinline__ void rotate_regs(V (&v)[NR], unsigned mask, const int (&cls)[RB],
-                                            R c0, R s0, R c1, R s1) {
+                                            R u0, R s0, R u1, R s1) {
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
         if (!((mask >> k) & 1u)) continue;
-        R c = cls[k] ? c1 : c0;
+        R u = cls[k] ? u1 : u0;
         R s = cls[k] ? s1 : s0;
 #pragma unroll
         for (int r = 0; r < NR; ++r)
-            if (!((r >> k) & 1)) xrot(v[r], v[r | (1 << k)], c, s);
+            if (!((r >> k) & 1)) xrot(v[r], v[r | (1 << k)], u, s);
     }
 }
 
@@ -112,7 +118,7 @@ __global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ ps
     for (int k = 0; k < nfixed; ++k)
         if ((tau >> k) & 1) base |= 1ll << d->fixed_pos[k];
 
-    const R c0 = (R)rec[0], s0 = (R)rec[1], c1 = (R)rec[2], s1 = (R)rec[3];
+    const R u0 = (R)rec[0], s0 = (R)rec[1], u1 = (R)rec[2], s1 = (R)rec[3];
     const int apply_z = d->apply_z;
     const int nB1 = d->nB + 1;
     if (apply_z) {
@@ -144,7 +150,7 @@ __global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ ps
         int cls[RB];
 #pragma unroll
         for (int k = 0; k < RB; ++k) cls[k] = d->reg_cls[0][k];
-        rotate_regs<R>(v, d->rot_mask[0], cls, c0, s0, c1, s1);
+        rotate_regs<R>(v, d->rot_mask[0], cls, u0, s0, u1, s1);
 #pragma unroll
         for (int r = 0; r < NR; ++r) tile[swz(t | (r << TB))] = v[r];
     }
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ ps
         int cls[RB];
 #pragma unroll
         for (int k = 0; k < RB; ++k) cls[k] = d->reg_cls[1][k];
-        rotate_regs<R>(v, d->rot_mask[1], cls, c0, s0, c1, s1);
+        rotate_regs<R>(v, d->rot_mask[1], cls, u0, s0, u1, s1);
 #pragma unroll
         for (int r = 0; r < NR; ++r) tile[swz(r | (t << RB))] = v[r];
         __syncthreads();
@@ -169,7 +175,7 @@ __global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ ps
         int cls[RB];
 #pragma unroll
         for (int k = 0; k < RB; ++k) cls[k] = d->reg_cls[2][k];
-        rotate_regs<R>(v, d->rot_mask[2], cls, c0, s0, c1, s1);
+        rotate_regs<R>(v, d->rot_mask[2], cls, u0, s0, u1, s1);
     }
     long long toff = base;
 #pragma unroll
@@ -199,7 +205,7 @@ __global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ ps
 #pragma unroll
             for (int k = 0; k < RB; ++k)
                 if ((r >> k) & 1) { a ^= ra[k]; b ^= rb[k]; }
-            v[r] = cmul(v[r], lut[__popc(a) * nB1 + __popc(b)]);
+            v[r] = cphase(v[r], lut[__popc(a) * nB1 + __popc(b)]);
         }
     }
 #pragma unroll
@@ -262,7 +268,7 @@ __global__ void __launch_bounds__(256) k_zdiag(typename C2<R>::T *__restrict__ p
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dim;
          i += (long long)gridDim.x * blockDim.x) {
         uint2 p = parity_of(tab, i, nbytes);
-        psi[i] = cmul(psi[i], lut[__popc(p.x) * nB1 + __popc(p.y)]);
+        psi[i] = cphase(psi[i], lut[__popc(p.x) * nB1 + __popc(p.y)]);
     }
 }
 
@@ -271,7 +277,7 @@ __global__ void __launch_bounds__(256) k_zdiag(typename C2<R>::T *__restrict__ p
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void k_rx(typename C2<R>::T *__restrict__ psi, int n, long long state_stride, int q,
-                     R c, R s) {
+                     R u, R s) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= (1ll << (n - 1))) return;
     psi += (long long)blockIdx.y * state_stride;
@@ -279,13 +285,13 @@ __global__ void k_rx(typename C2<R>::T *__restrict__ psi, int n, long long state
     long long i0 = ((p >> q) << (q + 1)) | lo;
     long long i1 = i0 | (1ll << q);
     auto a = psi[i0], b = psi[i1];
-    xrot(a, b, c, s);
+    xrot(a, b, u, s);
     psi[i0] = a; psi[i1] = b;
 }
 
 template <typename R>
 __global__ void k_xstring(typename C2<R>::T *__restrict__ psi, int n, long long state_stride,
-                          unsigned long long mask, int top, R c, R s) {
+                          unsigned long long mask, int top, R u, R s) {
     long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (p >= (1ll << (n - 1))) return;
     psi += (long long)blockIdx.y * state_stride;
@@ -293,22 +299,19 @@ __global__ void k_xstring(typename C2<R>::T *__restrict__ psi, int n, long long 
     long long i0 = ((p >> top) << (top + 1)) | lo;   // bit `top` of i0 is 0
     long long i1 = i0 ^ (long long)mask;
     auto a = psi[i0], b = psi[i1];
-    xrot(a, b, c, s);
+    xrot(a, b, u, s);
     psi[i0] = a; psi[i1] = b;
 }
 
+// amplitude i <- exp(i theta (-1)^{popcount(i & mask)}) amplitude i, cos theta = 1 - u
 template <typename R>
 __global__ void k_zterm(typename C2<R>::T *__restrict__ psi, int n, long long state_stride,
-                        unsigned long long mask, R c, R s) {
+                        unsigned long long mask, R u, R s) {
     long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (1ll << n)) return;
     psi += (long long)blockIdx.y * state_stride;
     R ss = (__popcll((unsigned long long)i & mask) & 1) ? -s : s;
-    auto a = psi[i];
-    typename C2<R>::T r;
-    r.x = c * a.x - ss * a.y;
-    r.y = c * a.y + ss * a.x;
-    psi[i] = r;
+    psi[i] = cphase(psi[i], mk<R>(u, ss));
 }
 
 template <typename R>

@@ -143,17 +143,51 @@ void build_passes(qs_sim *s) {
     }
 }
 
+// Rotation / phase coefficients for exp(i t P) = (1 - u) + i s P, u = 1 - cos t =
+// 2 sin^2(t/2), s = sin t, computed in FP64.  Keeping u instead of cos t keeps its
+// full relative precision for the small angles of a Trotter step, so the rounded
+// pair satisfies (1-u)^2 + s^2 = 1 to ~1e-10 instead of ~1e-7 (plain rounding of
+// cos t near 1).  For complex64 the float pair is then chosen, within +-3 ulps of
+// each component, to minimise |(1-u)^2 + s^2 - 1| evaluated in double; this keeps
+// rotations and phases from scaling the norm systematically step after step.
+void unit_pair(bool f32, double t, double *ou, double *os) {
+    double sh = sin(0.5 * t);
+    double u = 2.0 * sh * sh, s = sin(t);
+    if (!f32) { *ou = u; *os = s; return; }
+    auto err = [](float a, float b) {
+        double c = 1.0 - (double)a;
+        return fabs(c * c + (double)b * (double)b - 1.0);
+    };
+    float u0 = (float)u, s0 = (float)s;
+    float bu = u0, bs = s0;
+    double be = err(u0, s0);
+    double bd = 0.0;
+    float uu = u0;
+    for (int i = 0; i < 3; ++i) uu = nextafterf(uu, -4.0f);
+    for (int i = -3; i <= 3; ++i, uu = nextafterf(uu, 4.0f)) {
+        float ss = s0;
+        for (int j = 0; j < 3; ++j) ss = nextafterf(ss, -4.0f);
+        for (int j = -3; j <= 3; ++j, ss = nextafterf(ss, 4.0f)) {
+            double e = err(uu, ss);
+            double dd = fabs((double)uu - u) + fabs((double)ss - s);
+            if (e < be || (e == be && dd < bd)) { be = e; bd = dd; bu = uu; bs = ss; }
+        }
+    }
+    *ou = bu; *os = bs;
+}
+
 void fill_record(const qs_sim *s, const Op &op, double *r) {
-    r[0] = cos(op.thx[0]); r[1] = sin(op.thx[0]);
-    r[2] = cos(op.thx[1]); r[3] = sin(op.thx[1]);
+    const bool f32 = s->dtype == QS_C64;
+    unit_pair(f32, op.thx[0], &r[0], &r[1]);
+    unit_pair(f32, op.thx[1], &r[2], &r[3]);
     if (!op.has_z) return;
     const int nA = s->nA, nB = s->nB;
     for (int a = 0; a <= nA; ++a)
         for (int b = 0; b <= nB; ++b) {
             // exp(i [zA * sum_p (-1)^{pi_p} + zB * sum_b (-1)^{pi_b}]) with a odd plaquettes, b odd bonds
             double phi = op.zA * (double)(nA - 2 * a) + op.zB * (double)(nB - 2 * b);
-            r[4 + 2 * (a * (nB + 1) + b)] = cos(phi);
-            r[5 + 2 * (a * (nB + 1) + b)] = sin(phi);
+            int e = a * (nB + 1) + b;
+            unit_pair(f32, phi, &r[4 + 2 * e], &r[5 + 2 * e]);
         }
 }
 
@@ -260,9 +294,10 @@ qs_status run_op_fused(qs_sim *s, const Op *ops_b, const double *drec) {
         for (int b = 0; b < s->batch; ++b) {
             V<R> *psi = (V<R> *)s->state[0] + (long long)b * s->dim;
             for (int q = 0; q < s->n; ++q) {
-                double th = ops_b[b].thx[s->lat.x_class[q]];
+                double c, sn;   // (u, s)
+                unit_pair(sizeof(R) == 4, ops_b[b].thx[s->lat.x_class[q]], &c, &sn);
                 k_rx<R><<<grid_for(s->dim / 2, 256), 256, 0, s->stream>>>(psi, s->n, s->dim, q,
-                                                                            (R)cos(th), (R)sin(th));
+                                                                            (R)c, (R)sn);
                 CKL(s); s->launches++;
             }
         }
@@ -275,11 +310,12 @@ qs_status run_op_fused(qs_sim *s, const Op *ops_b, const double *drec) {
     if (ug) {
         for (int b = 0; b < s->batch; ++b) {
             V<R> *psi = (V<R> *)s->state[0] + (long long)b * s->dim;
-            double th = ops_b[b].thx[1];
+            double c, sn;
+            unit_pair(sizeof(R) == 4, ops_b[b].thx[1], &c, &sn);
             for (uint64_t m : s->lat.stars) {
                 int top = 63 - __builtin_clzll(m);
                 k_xstring<R><<<grid_for(s->dim / 2, 256), 256, 0, s->stream>>>(
-                    psi, s->n, s->dim, (unsigned long long)m, top, (R)cos(th), (R)sin(th));
+                    psi, s->n, s->dim, (unsigned long long)m, top, (R)c, (R)sn);
                 CKL(s); s->launches++;
             }
         }
@@ -295,30 +331,35 @@ qs_status run_op_pergate(qs_sim *s, const Op *ops_b) {
     for (int b = 0; b < s->batch; ++b) {
         const Op &o = ops_b[b];
         V<R> *psi = (V<R> *)s->state[0] + (long long)b * s->dim;
+        const bool f32 = sizeof(R) == 4;
+        double cx[2], sx[2], ca, sa, cb, sb;
+        unit_pair(f32, o.thx[0], &cx[0], &sx[0]);
+        unit_pair(f32, o.thx[1], &cx[1], &sx[1]);
+        unit_pair(f32, o.zA, &ca, &sa);
+        unit_pair(f32, o.zB, &cb, &sb);
         for (int q = 0; q < s->n; ++q) {
-            double th = o.thx[s->lat.x_class[q]];
+            int k = s->lat.x_class[q];
             k_rx<R><<<grid_for(s->dim / 2, 256), 256, 0, s->stream>>>(psi, s->n, s->dim, q,
-                                                                        (R)cos(th), (R)sin(th));
+                                                                        (R)cx[k], (R)sx[k]);
             CKL(s); s->launches++;
         }
         if (!s->lat.gauge_higgs) {
-            double th = o.thx[1];
             for (uint64_t m : s->lat.stars) {
                 int top = 63 - __builtin_clzll(m);
                 k_xstring<R><<<grid_for(s->dim / 2, 256), 256, 0, s->stream>>>(
-                    psi, s->n, s->dim, (unsigned long long)m, top, (R)cos(th), (R)sin(th));
+                    psi, s->n, s->dim, (unsigned long long)m, top, (R)cx[1], (R)sx[1]);
                 CKL(s); s->launches++;
             }
         }
         if (o.has_z) {
             for (uint64_t m : s->lat.plaquettes) {
                 k_zterm<R><<<grid_for(s->dim, 256), 256, 0, s->stream>>>(
-                    psi, s->n, s->dim, (unsigned long long)m, (R)cos(o.zA), (R)sin(o.zA));
+                    psi, s->n, s->dim, (unsigned long long)m, (R)ca, (R)sa);
                 CKL(s); s->launches++;
             }
             for (uint64_t m : s->lat.second) {
                 k_zterm<R><<<grid_for(s->dim, 256), 256, 0, s->stream>>>(
-                    psi, s->n, s->dim, (unsigned long long)m, (R)cos(o.zB), (R)sin(o.zB));
+                    psi, s->n, s->dim, (unsigned long long)m, (R)cb, (R)sb);
                 CKL(s); s->launches++;
             }
         }
