@@ -85,7 +85,11 @@ typedef enum {
                                  this many steps and at the end (0 = never; default 0) */
     QS_OPT_PROFILE = 2,       /* 1: time every fused X-pass launch with CUDA events on
                                  the bound stream (read with qs_profile_read)        */
-    QS_OPT_GRAPH = 3          /* 1: qs_evolve replays its launches as a CUDA graph    */
+    QS_OPT_GRAPH = 3,         /* 1: qs_evolve replays its launches as a CUDA graph    */
+    QS_OPT_XPASS = 4,         /* X-pass kernel for complex64: 0 auto (TMA), 1 the
+                                 register-staged kernel, 2 the persistent TMA kernel */
+    QS_OPT_TMA_BUFFERS = 5    /* shared-memory tile buffers per CTA of the TMA kernel:
+                                 2 (default) or 3                                    */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open
@@ -137,6 +141,10 @@ qs_status qs_expect_pauli(qs_sim *sim, int type, uint64_t mask, double *out);
 /* |<phi|psi>|^2 per batch element; ref_dev_state has the layout of the bound
  * state (same dtype, batch and size). out: host [batch]. */
 qs_status qs_fidelity(qs_sim *sim, const void *ref_dev_state, double *out);
+
+/* Synchronise the bound stream and report device-side failures: QS_ERR_CUDA for
+ * a failed launch, QS_ERR_TIMEOUT if a bounded wait inside a kernel gave up. */
+qs_status qs_sync(qs_sim *sim);
 
 /* Total milliseconds and launch count of the fused X-pass kernel since the last
  * read, when QS_OPT_PROFILE is on.  Synchronises the stream. */

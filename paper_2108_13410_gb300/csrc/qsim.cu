@@ -12,9 +12,12 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "qsim.h"
 #include "lattice.h"
 #include "kernels.cuh"
+#include "xpass_tma.cuh"
 
 using namespace qsim;
 
@@ -64,6 +67,14 @@ struct qs_sim {
     // profiling of the fused pass
     std::vector<cudaEvent_t> ev_pool; size_t ev_used = 0;
     long long launches = 0;
+    // persistent TMA X pass (complex64)
+    int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
+    int nbuf = 2;                          // TMA shared-memory buffers per CTA (2 or 3)
+    int sm_count = 0;
+    std::vector<TmaPass> tpasses;          // [2 * pass + apply_z]
+    std::vector<CUtensorMap> tmaps;        // one per pass, encoded for the bound state
+    bool tmaps_ok = false;
+    int *d_err = nullptr;                  // device flag: bounded wait gave up
 };
 
 #define FAIL(sim, code, ...)                                   \
@@ -141,6 +152,99 @@ void build_passes(qs_sim *s) {
         s->passes.push_back(d);
         next = first ? LT : next + k;
     }
+}
+
+// TMA pass descriptors derived from the pass plan (local bit j < c is global j;
+// local bit j >= c is global next + j - c).
+void build_tma_passes(qs_sim *s) {
+    s->tpasses.clear();
+    const int n = s->n;
+    for (const PassDesc &d : s->passes) {
+        int c = 0;
+        while (c < LT && d.lmap[c] == c) ++c;
+        const bool first = (c == LT);
+        const int next = first ? LT : d.lmap[c];
+        const int k = LT - c;
+        if (first) c = LT;
+        auto g = [&](int local) -> int { return local < c ? local : next + (local - c); };
+        TmaPass P;
+        memset(&P, 0, sizeof(P));
+        P.c = c; P.next = first ? LT : next; P.k = first ? 0 : k;
+        P.mid_bits = P.next - P.c;
+        P.total_tiles = (long long)s->batch << (n - LT);
+        const int thr_local[8] = {0, 1, 2, 3, 8, 9, 10, 11};
+        for (int j = 0; j < 8; ++j) {
+            int q = g(thr_local[j]);
+            P.toff_c[j] = 1ll << q;
+            P.pa_thr[j] = d.colA[q]; P.pb_thr[j] = d.colB[q];
+        }
+        for (int r = 0; r < NR; ++r) {
+            long long off = 0; uint32_t a = 0, b = 0;
+            for (int kk = 0; kk < RB; ++kk)
+                if ((r >> kk) & 1) { int q = g(4 + kk); off += 1ll << q; a ^= d.colA[q]; b ^= d.colB[q]; }
+            P.roff_c[r] = off; P.pa_reg[r] = a; P.pb_reg[r] = b;
+        }
+        const int stage_base[3] = {8, 0, 4};
+        for (int st = 0; st < 3; ++st) {
+            unsigned cl = 0;
+            for (int kk = 0; kk < RB; ++kk)
+                if (s->lat.x_class[g(stage_base[st] + kk)]) cl |= 1u << kk;
+            P.cls[st] = cl;
+            P.rot[st] = d.rot_mask[st];
+        }
+        P.stage_b = P.rot[1] != 0;
+        P.nA = s->nA; P.nB = s->nB;
+        P.tile_bits = n - LT;
+        for (int i = 0; i < P.tile_bits && i < 32; ++i) {
+            int q = i < P.mid_bits ? P.c + i : P.next + P.k + (i - P.mid_bits);
+            P.pa_tile[i] = d.colA[q]; P.pb_tile[i] = d.colB[q];
+        }
+        TmaPass Z = P; Z.apply_z = 1;
+        P.apply_z = 0;
+        s->tpasses.push_back(P);
+        s->tpasses.push_back(Z);
+    }
+}
+
+// Encode one 5-D tensor map per pass over the bound complex64 state:
+//   dims (8-byte elements) {16, 2^(c-4), 2^(next-c), 2^k, 2^(n-next-k) * batch},
+//   box {16, 2^(c-4), 1, 2^k, 1}, 128-byte swizzle.
+qs_status encode_tmaps(qs_sim *s) {
+    s->tmaps_ok = false;
+    s->tmaps.clear();
+    if (s->dtype != QS_C64 || s->passes.empty() || !s->state[0]) return QS_OK;
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            FAIL(s, QS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const int n = s->n;
+    for (size_t p = 0; p < s->passes.size(); ++p) {
+        const TmaPass &P = s->tpasses[2 * p];
+        cuuint64_t dims[5] = {16, 1ull << (P.c - 4), 1ull << (P.next - P.c), 1ull << P.k,
+                              (1ull << (n - P.next - P.k)) * (cuuint64_t)s->batch};
+        cuuint64_t strides[4] = {16 * 8, (1ull << P.c) * 8, (1ull << P.next) * 8, (1ull << (P.next + P.k)) * 8};
+        cuuint32_t box[5] = {16, (cuuint32_t)(1u << (P.c - 4)), 1, (cuuint32_t)(1u << P.k), 1};
+        cuuint32_t es[5] = {1, 1, 1, 1, 1};
+        CUtensorMap m;
+        CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, s->state[0], dims, strides, box, es,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) FAIL(s, QS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for pass %zu", (int)r, p);
+        s->tmaps.push_back(m);
+    }
+    s->tmaps_ok = true;
+    return QS_OK;
+}
+
+size_t tma_smem_bytes(const qs_sim *s, int nbuf, bool z) {
+    size_t b = (size_t)nbuf * TMA_TILE_BYTES + 1024;
+    if (z) b += (size_t)(s->nA + 1) * (s->nB + 1) * 8 + 3 * 256 * 8;
+    return b;
 }
 
 // Rotation / phase coefficients for exp(i t P) = (1 - u) + i s P, u = 1 - cos t =
@@ -258,8 +362,27 @@ qs_status launch_xpass(qs_sim *s, int p, bool apply_z, const double *rec) {
         s->ev_used += 2;
         CK(s, cudaEventRecord(e0, s->stream));
     }
-    k_xpass<R><<<grid, NT, smem, s->stream>>>((V<R> *)s->state[0], s->dim, rec, s->rec_stride,
-                                               s->d_passes + 2 * p + (apply_z ? 1 : 0));
+    const bool tma = sizeof(R) == 4 && s->tmaps_ok && s->xpass_impl != 1;
+    if (tma) {
+        const TmaPass &P = s->tpasses[2 * p + (apply_z ? 1 : 0)];
+        size_t sm = tma_smem_bytes(s, s->nbuf, apply_z);
+        int per_sm = 0;
+        if (s->nbuf == 3)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_tma<3>, NT, sm);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_tma<2>, NT, sm);
+        if (per_sm < 1) per_sm = 1;
+        long long g = std::min<long long>(P.total_tiles, (long long)per_sm * s->sm_count);
+        if (s->nbuf == 3)
+            k_xpass_tma<3><<<(unsigned)g, NT, sm, s->stream>>>((float2 *)s->state[0], rec, s->rec_stride,
+                                                               1ll << (s->n - LT), s->d_err, s->tmaps[p], P);
+        else
+            k_xpass_tma<2><<<(unsigned)g, NT, sm, s->stream>>>((float2 *)s->state[0], rec, s->rec_stride,
+                                                               1ll << (s->n - LT), s->d_err, s->tmaps[p], P);
+    } else {
+        k_xpass<R><<<grid, NT, smem, s->stream>>>((V<R> *)s->state[0], s->dim, rec, s->rec_stride,
+                                                   s->d_passes + 2 * p + (apply_z ? 1 : 0));
+    }
     CKL(s);
     s->launches++;
     if (s->profile) CK(s, cudaEventRecord(e1, s->stream));
@@ -395,10 +518,22 @@ qs_status reduce_xmask(qs_sim *s, const void *a, const void *b, uint64_t mask, i
     return QS_OK;
 }
 
+qs_status check_device_flag(qs_sim *s) {
+    int flag = 0;
+    CK(s, cudaMemcpy(&flag, s->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        cudaMemset(s->d_err, 0, sizeof(int));
+        FAIL(s, QS_ERR_TIMEOUT, "a bounded device wait gave up (flag %d)", flag);
+    }
+    return QS_OK;
+}
+
 qs_status read_results(qs_sim *s, int slots) {
     size_t bytes = (size_t)slots * s->batch * RED_NV * sizeof(double);
     CK(s, cudaMemcpyAsync(s->h_res, s->d_res, bytes, cudaMemcpyDeviceToHost, s->stream));
     CK(s, cudaStreamSynchronize(s->stream));
+    qs_status st = check_device_flag(s);
+    if (st != QS_OK) return st;
     for (size_t i = 0; i < (size_t)slots * s->batch * RED_NV; ++i)
         if (!std::isfinite(s->h_res[i])) FAIL(s, QS_ERR_NONFINITE, "non-finite reduction result");
     return QS_OK;
@@ -523,6 +658,7 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
     if (s->nA > 32 || s->nB > 32) { g_create_error = "more than 32 terms in a Z class"; delete s; return QS_ERR_ARG; }
     s->rec_stride = record_doubles(s->nA, s->nB);
     build_passes(s);
+    build_tma_passes(s);
     auto fail = [&](const char *what) {
         g_create_error = what;
         qs_destroy(s);
@@ -553,6 +689,18 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
     if (cudaMalloc((void **)&s->d_res, rbytes) != cudaSuccess) return fail("results");
     if (cudaMallocHost((void **)&s->h_res, rbytes) != cudaSuccess) return fail("pinned results");
     if (cudaEventCreateWithFlags(&s->rec_done, cudaEventDisableTiming) != cudaSuccess) return fail("event");
+    if (cudaMalloc((void **)&s->d_err, sizeof(int)) != cudaSuccess) return fail("error flag");
+    if (cudaMemset(s->d_err, 0, sizeof(int)) != cudaSuccess) return fail("error flag");
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (s->sm_count < 1) s->sm_count = 1;
+        cudaFuncSetAttribute(k_xpass_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(s, 2, true));
+        cudaFuncSetAttribute(k_xpass_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(s, 3, true));
+    }
     size_t smem64 = (size_t)(1 << LT) * 16 + (size_t)(s->nA + 1) * (s->nB + 1) * 16;
     cudaFuncSetAttribute(k_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
     cudaFuncSetAttribute(k_xpass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
@@ -569,6 +717,7 @@ void qs_destroy(qs_sim *s) {
     cudaFree(s->d_rec);
     cudaFree(s->d_partials);
     cudaFree(s->d_res);
+    cudaFree(s->d_err);
     if (s->h_rec) cudaFreeHost(s->h_rec);
     if (s->h_res) cudaFreeHost(s->h_res);
     if (s->rec_done) cudaEventDestroy(s->rec_done);
@@ -595,6 +744,7 @@ qs_status qs_bind_state(qs_sim *s, int slot, void *ptr, size_t bytes) {
     if (bytes < qs_state_bytes(s)) FAIL(s, QS_ERR_ARG, "buffer of %zu bytes < %zu", bytes, qs_state_bytes(s));
     s->state[slot] = ptr;
     s->state_cap[slot] = bytes;
+    if (slot == 0) return encode_tmaps(s);
     return QS_OK;
 }
 
@@ -615,6 +765,12 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
             s->renorm_every = (int)value; return QS_OK;
         case QS_OPT_PROFILE: s->profile = value != 0; return QS_OK;
         case QS_OPT_GRAPH: s->use_graph = value != 0; return QS_OK;
+        case QS_OPT_XPASS:
+            if (value < 0 || value > 2) FAIL(s, QS_ERR_ARG, "xpass kernel must be 0 (auto), 1 or 2");
+            s->xpass_impl = (int)value; return QS_OK;
+        case QS_OPT_TMA_BUFFERS:
+            if (value != 2 && value != 3) FAIL(s, QS_ERR_ARG, "TMA buffers must be 2 or 3");
+            s->nbuf = (int)value; return QS_OK;
         default: FAIL(s, QS_ERR_ARG, "unknown option %d", key);
     }
 }
@@ -794,6 +950,13 @@ qs_status qs_fidelity(qs_sim *s, const void *ref, double *out) {
         out[b] = re * re + im * im;
     }
     return QS_OK;
+}
+
+qs_status qs_sync(qs_sim *s) {
+    if (!s) return QS_ERR_ARG;
+    CK(s, cudaStreamSynchronize(s->stream));
+    CK(s, cudaGetLastError());
+    return check_device_flag(s);
 }
 
 qs_status qs_profile_read(qs_sim *s, double *total_ms, long long *count) {

@@ -1,0 +1,258 @@
+// xpass_tma.cuh -- persistent, TMA-fed X pass for complex64 states (sm_103a).
+//
+// Same operator as k_xpass (exp(i theta_q X_q) on the 12 local qubits of a
+// 4096-amplitude tile, optionally followed by the whole diagonal Z layer), but:
+//   * tiles arrive by cp.async.bulk.tensor (TMA) into shared memory, described by a
+//     5-D tensor map whose box is the tile (16 contiguous amplitudes x the chunk and
+//     new-qubit dimensions), with the 128-byte swizzle;
+//   * the grid is persistent: each CTA walks tiles blockIdx.x, +gridDim.x, ... with
+//     NBUF shared-memory buffers, so the TMA load of the next tiles overlaps the
+//     butterflies of the current one (mbarrier-tracked, bounded waits);
+//   * every per-pass constant (offsets, parity columns, rotation masks) is a
+//     __grid_constant__ kernel parameter, read from the constant bank.
+// Stage layouts (local bit -> register / thread), as in k_xpass:
+//   A: registers local {8..11}, threads local {0..7}           (8-byte smem access)
+//   B: registers local {0..3},  threads local {4..11}          (16-byte smem access)
+//   C: registers local {4..7},  threads local {0..3, 8..11}    (global store)
+// With the 128-byte swizzle, amplitude l sits at l ^ (((l >> 4) & 7) << 1): every
+// stage then hits 16 distinct banks per half-warp (8-byte) or 8 distinct 16-byte
+// units per quarter-warp (16-byte).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace qsim {
+
+struct TmaPass {
+    int c;                      // chunk bits (global bits 0..c-1 stay local bits 0..c-1)
+    int next;                   // first new global bit (local bit c)
+    int k;                      // new bits in this pass
+    int mid_bits;               // next - c: tile-index bits that land on global bits c..next-1
+    long long total_tiles;      // batch * 2^(n - 12)
+    long long toff_c[8];        // stage C: global offset of thread bit j (local 0,1,2,3,8,9,10,11)
+    long long roff_c[NR];       // stage C: global offset of register r (local bits 4..7)
+    unsigned rot[3];            // register bits to rotate in stages A, B, C
+    unsigned cls[3];            // register bit k of stage s uses class (cls[s] >> k) & 1
+    int stage_b;                // run stage B
+    int apply_z, nA, nB;
+    uint32_t pa_thr[8], pb_thr[8];    // parity columns of the stage-C thread bits
+    uint32_t pa_reg[NR], pb_reg[NR];  // parity of stage-C register r
+    uint32_t pa_tile[32], pb_tile[32];// parity columns of tile-index bits (bit order of tau)
+    int tile_bits;              // tile-index bits that carry parity (not batch)
+};
+
+constexpr int TMA_TILE_BYTES = (1 << LT) * 8;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~max_cycles SM clocks (about a second) and reports it.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long max_cycles) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > max_cycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2, int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ int swz128(int l) { return l ^ (((l >> 4) & 7) << 1); }
+
+template <int NBUF>
+__global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__restrict__ psi, const double *__restrict__ recs,
+                                                  int rec_stride, long long tiles_per_state,
+                                                  int *__restrict__ err_flag,
+                                                  const __grid_constant__ CUtensorMap tmap,
+                                                  const __grid_constant__ TmaPass P) {
+    extern __shared__ unsigned char smem_raw[];
+    // 1024-byte alignment for the 128-byte swizzle pattern
+    unsigned char *base_ptr = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float2 *buf = reinterpret_cast<float2 *>(base_ptr);                       // NBUF x 4096
+    float2 *lut = buf + NBUF * (1 << LT);                                       // (nA+1)(nB+1)
+    uint2 *ptab = reinterpret_cast<uint2 *>(lut + (P.apply_z ? (P.nA + 1) * (P.nB + 1) : 0));  // 3 x 256
+    __shared__ uint64_t bars[NBUF];
+    __shared__ int s_ok;
+
+    const int t = threadIdx.x;
+    const long long G = gridDim.x;
+    const long long T = P.total_tiles;
+    const long long first = blockIdx.x;
+    const long long max_wait = 2000000000ll;   // SM cycles (~1 s)
+
+    if (t == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
+    }
+    // per-CTA tables: parity of tile-index bytes, Z phase table (batch 0 record; the
+    // record of other batch elements is loaded when the batch index changes)
+    if (P.apply_z) {
+        for (int e = t; e < 3 * 256; e += NT) {
+            int byte = e >> 8, val = e & 255;
+            uint32_t a = 0, b = 0;
+            for (int j = 0; j < 8; ++j) {
+                int bit = 8 * byte + j;
+                if (bit < P.tile_bits && ((val >> j) & 1)) { a ^= P.pa_tile[bit]; b ^= P.pb_tile[bit]; }
+            }
+            ptab[e] = make_uint2(a, b);
+        }
+    }
+    __syncthreads();
+
+    auto coords_of = [&](long long tile, int &x1, int &x2, int &x4) {
+        x1 = 0;
+        x2 = (int)(tile & ((1ll << P.mid_bits) - 1));
+        x4 = (int)(tile >> P.mid_bits);
+    };
+    auto issue = [&](long long it) {
+        long long tile = first + it * G;
+        int b = (int)(it % NBUF);
+        int x1, x2, x4;
+        coords_of(tile, x1, x2, x4);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&bars[b], TMA_TILE_BYTES);
+        tma_load_5d(buf + (size_t)b * (1 << LT), &tmap, &bars[b], 0, x1, x2, 0, x4);
+    };
+
+    long long n_my = (T - first + G - 1) / G;   // tiles this CTA processes
+    if (first >= T) n_my = 0;
+    if (t == 0)
+        for (long long it = 0; it < NBUF - 1 && it < n_my; ++it) issue(it);
+
+    // per-thread constants of stage C
+    const int tlo = t & 15, thi = t >> 4;
+    long long toff = 0;
+    uint32_t pa_t = 0, pb_t = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if ((tlo >> j) & 1) { toff += P.toff_c[j]; pa_t ^= P.pa_thr[j]; pb_t ^= P.pb_thr[j]; }
+        if ((thi >> j) & 1) { toff += P.toff_c[4 + j]; pa_t ^= P.pa_thr[4 + j]; pb_t ^= P.pb_thr[4 + j]; }
+    }
+    const int nB1 = P.nB + 1;
+    const int nlut = (P.nA + 1) * nB1;
+    long long cur_batch = -1;
+    float u0 = 0.f, s0 = 0.f, u1 = 0.f, s1 = 0.f;
+
+    for (long long it = 0; it < n_my; ++it) {
+        const long long tile = first + it * G;
+        const int b = (int)(it % NBUF);
+        const uint32_t parity = (uint32_t)((it / NBUF) & 1);
+        const long long batch = tile / tiles_per_state;
+        if (batch != cur_batch) {
+            // operator record of this batch element (angles, Z table)
+            __syncthreads();
+            const double *rec = recs + batch * rec_stride;
+            u0 = (float)rec[0]; s0 = (float)rec[1]; u1 = (float)rec[2]; s1 = (float)rec[3];
+            if (P.apply_z)
+                for (int i = t; i < nlut; i += NT) lut[i] = make_float2((float)rec[4 + 2 * i], (float)rec[5 + 2 * i]);
+            cur_batch = batch;
+        }
+        if (t == 0) {
+            if (!mbar_wait_bounded(&bars[b], parity, max_wait)) {
+                atomicOr(err_flag, 1);
+                s_ok = 0;
+                // wait (bounded) for every load this CTA still has in flight before leaving
+                for (long long j = it; j < it + NBUF - 1 && j < n_my; ++j)
+                    mbar_wait_bounded(&bars[j % NBUF], (uint32_t)((j / NBUF) & 1), max_wait);
+            }
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        if (t == 0 && it + NBUF - 1 < n_my) issue(it + NBUF - 1);
+
+        float2 *tb = buf + (size_t)b * (1 << LT);
+        float2 v[NR];
+        // ---- stage A: registers = local 8..11 ----
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = tb[swz128(t | (r << TB))];
+        {
+            int cls[RB];
+#pragma unroll
+            for (int kk = 0; kk < RB; ++kk) cls[kk] = (P.cls[0] >> kk) & 1;
+            rotate_regs<float>(v, P.rot[0], cls, u0, s0, u1, s1);
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) tb[swz128(t | (r << TB))] = v[r];
+        __syncthreads();
+        // ---- stage B: registers = local 0..3 (16-byte accesses) ----
+        if (P.stage_b) {
+            float4 *tb4 = reinterpret_cast<float4 *>(tb);
+#pragma unroll
+            for (int m = 0; m < NR / 2; ++m) {
+                float4 q = tb4[swz128((2 * m) | (t << RB)) >> 1];
+                v[2 * m] = make_float2(q.x, q.y);
+                v[2 * m + 1] = make_float2(q.z, q.w);
+            }
+            int cls[RB];
+#pragma unroll
+            for (int kk = 0; kk < RB; ++kk) cls[kk] = (P.cls[1] >> kk) & 1;
+            rotate_regs<float>(v, P.rot[1], cls, u0, s0, u1, s1);
+#pragma unroll
+            for (int m = 0; m < NR / 2; ++m)
+                tb4[swz128((2 * m) | (t << RB)) >> 1] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x,
+                                                                    v[2 * m + 1].y);
+            __syncthreads();
+        }
+        // ---- stage C: registers = local 4..7; Z layer; store ----
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = tb[swz128(tlo | (r << 4) | (thi << 8))];
+        {
+            int cls[RB];
+#pragma unroll
+            for (int kk = 0; kk < RB; ++kk) cls[kk] = (P.cls[2] >> kk) & 1;
+            rotate_regs<float>(v, P.rot[2], cls, u0, s0, u1, s1);
+        }
+        // global base of the tile: mid bits -> global c.., upper bits (and batch) -> next+k..
+        const long long tib = tile;
+        const long long mid = tib & ((1ll << P.mid_bits) - 1);
+        const long long up = tib >> P.mid_bits;
+        const long long gbase = (mid << P.c) + (up << (P.next + P.k));
+        if (P.apply_z) {
+            const long long tin = tile - batch * tiles_per_state;   // parity ignores batch
+            uint2 e0 = ptab[tin & 255], e1 = ptab[256 + ((tin >> 8) & 255)], e2 = ptab[512 + ((tin >> 16) & 255)];
+            const uint32_t pa = pa_t ^ e0.x ^ e1.x ^ e2.x;
+            const uint32_t pb = pb_t ^ e0.y ^ e1.y ^ e2.y;
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                v[r] = cphase(v[r], lut[__popc(pa ^ P.pa_reg[r]) * nB1 + __popc(pb ^ P.pb_reg[r])]);
+        }
+        float2 *dst = psi + gbase + toff;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) dst[P.roff_c[r]] = v[r];
+    }
+}
+
+}  // namespace qsim

@@ -22,7 +22,7 @@ QS_PERIODIC, QS_OPEN = 0, 1
 QS_GAUGE_HIGGS, QS_UNITARY_GAUGE = 0, 1
 QS_C64, QS_C128 = 0, 1
 QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
-QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH = range(4)
+QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS = range(6)
 
 
 class QsError(RuntimeError):
@@ -63,6 +63,7 @@ _SIGS = {
     "qs_expect": ([_P, _I, _I, _CP, _D, _DP], _I),
     "qs_expect_pauli": ([_P, _I, _U64, _DP], _I),
     "qs_fidelity": ([_P, _P, _DP], _I),
+    "qs_sync": ([_P], _I),
     "qs_profile_read": ([_P, _DP, ctypes.POINTER(_LL)], _I),
     "qs_launch_count": ([_P], _LL),
 }
@@ -195,6 +196,10 @@ def qs_fidelity(sim, ref_dev_ptr: int, batch: int = 1):
     return out
 
 
+def qs_sync(sim):
+    _check(sim, library().qs_sync(sim))
+
+
 def qs_profile_read(sim):
     ms = ctypes.c_double()
     cnt = _LL()
@@ -296,6 +301,9 @@ class Simulator:
             host_tensor = self.torch.empty(self.state.shape, dtype=self.state.dtype, pin_memory=True)
         qs_download_state(self.h, host_tensor.data_ptr(), self.state_bytes)
         return host_tensor
+
+    def sync(self):
+        qs_sync(self.h)
 
     def profile_read(self):
         return qs_profile_read(self.h)

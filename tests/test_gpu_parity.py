@@ -246,3 +246,25 @@ def test_errors_are_reported():
     with pytest.raises(Q.QsError) as e:
         sim.expect(0)
     assert e.value.status == 4      # QS_ERR_NONFINITE
+
+
+@gpu
+@pytest.mark.parametrize("impl,nbuf", [(1, 2), (2, 2), (2, 3)])
+def test_complex64_xpass_kernels_agree(impl, nbuf):
+    """The register-staged and the persistent TMA X-pass kernels (2 or 3 tile
+    buffers) give the oracle's amplitudes on a 20-qubit lattice with batch 2."""
+    from paper_2108_13410_gb300 import QS_OPT_XPASS, QS_OPT_TMA_BUFFERS
+    lat = OracleLattice(2, 5, True, "ug")          # 20 link qubits, 256 tiles per state
+    couplings = [(0.6, 0.6), (1.1, 0.3)]
+    T, n = 2.0, 12
+    s = O.schedule_linear(T, n)
+    sim = _sim(2, 5, form="ug", dtype="c64", batch=2)
+    sim.set_option(QS_OPT_XPASS, impl)
+    sim.set_option(QS_OPT_TMA_BUFFERS, nbuf)
+    sim.init_plus()
+    sim.evolve(couplings, s, T / n, 2)
+    sim.sync()
+    got = sim.download().numpy()
+    for b, (g, lam) in enumerate(couplings):
+        ref = O.evolve(lat, Couplings(g, lam), s, T / n, 2)
+        _assert_amplitudes(got[b], ref, "c64")
