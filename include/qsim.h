@@ -152,6 +152,37 @@ qs_status qs_profile_read(qs_sim *sim, double *total_ms, long long *launches);
 /* Number of kernels this library launched since the last call (all kinds). */
 long long qs_launch_count(qs_sim *sim);
 
+/* Largest batch accepted by qs_expect_z_noalloc. */
+#define QS_NOALLOC_MAX_BATCH 16
+
+/* Norm and Z-string expectation without any memory allocation.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate device
+ * memory, e.g. code running while a stream is captured into a CUDA graph
+ * (cudaMalloc is not a stream operation and cannot be captured), hosts that give
+ * all device memory to their own pool, or loops where the device-wide
+ * synchronisation of cudaMalloc is not acceptable.
+ *
+ * For each of `batch` states of 2^n_qubits amplitudes (layout of qs_bind_state,
+ * dtype QS_C64 or QS_C128) at state_dev, writes out_dev[2b] = <psi_b|psi_b> and
+ * out_dev[2b + 1] = <psi_b|Z_mask|psi_b> (FP64, device memory supplied by the
+ * caller), stream-ordered on `stream` (cudaStream_t as void*, NULL = legacy default).
+ * Nothing is synchronised; read out_dev after the stream has completed.
+ *
+ * No qs_sim handle is needed and nothing is allocated: the block partial sums live
+ * in one fixed device array of QS_NOALLOC_MAX_BATCH * 304 * 2 doubles (77,824
+ * bytes), held by every GPU that loads the library until the process exits.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  All calls on a device share the array, which keeps the last
+ * call's partial sums (each call overwrites every slot it later reads, so nothing
+ * needs clearing); calls whose kernels overlap on the GPU, e.g. on two streams at
+ * once, race on it.  Errors: QS_ERR_ARG for a null pointer, n_qubits outside
+ * [1, 34], a bad dtype, batch outside [1, QS_NOALLOC_MAX_BATCH] or mask bits
+ * beyond n_qubits; QS_ERR_CUDA if a launch fails.  qs_last_error(NULL) gives the
+ * message. */
+qs_status qs_expect_z_noalloc(const void *state_dev, int n_qubits, int dtype, int batch,
+                              uint64_t zmask, double *out_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

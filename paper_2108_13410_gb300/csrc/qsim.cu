@@ -44,6 +44,11 @@ inline Coef coefficients(const qs_couplings &c, double s) {
 
 }  // namespace
 
+namespace qsim {
+// Message reported by qs_last_error(NULL): the last failed qs_create or handle-free call.
+void set_handle_free_error(const std::string &msg) { g_create_error = msg; }
+}
+
 struct qs_sim {
     Lattice lat;
     int boundary = 0, form = 0, dtype = 0, batch = 1, n = 0;

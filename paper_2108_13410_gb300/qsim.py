@@ -66,6 +66,7 @@ _SIGS = {
     "qs_sync": ([_P], _I),
     "qs_profile_read": ([_P, _DP, ctypes.POINTER(_LL)], _I),
     "qs_launch_count": ([_P], _LL),
+    "qs_expect_z_noalloc": ([_P, _I, _I, _I, _U64, _P, _P], _I),
 }
 
 
@@ -209,6 +210,14 @@ def qs_profile_read(sim):
 
 def qs_launch_count(sim) -> int:
     return library().qs_launch_count(sim)
+
+
+def qs_expect_z_noalloc(state_dev_ptr: int, n_qubits: int, dtype: int, batch: int, zmask: int,
+                        out_dev_ptr: int, stream_handle: int = 0):
+    """Norm and <Z_mask> per batch element into caller-owned device memory
+    out[2b], out[2b+1], with no allocation (see include/qsim.h)."""
+    _check(None, library().qs_expect_z_noalloc(state_dev_ptr, n_qubits, dtype, batch, zmask,
+                                               out_dev_ptr, stream_handle))
 
 
 # ---------------------------------------------------------------------------
