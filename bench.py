@@ -46,21 +46,28 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_hash() -> str:
+    """sha256 (16 hex digits) of the X-pass kernel sources."""
+    import hashlib
+    d = hashlib.sha256()
+    for f in ("kernels.cuh", "xpass_tma.cuh"):
+        d.update(open(os.path.join(ROOT, "paper_2108_13410_gb300", "csrc", f), "rb").read())
+    return d.hexdigest()[:16]
+
+
 def profile_traffic(kernel_tag: str):
     """dram read+write bytes per launch from the committed ncu summary, if it was
     taken on the current kernel source."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
     if not os.path.exists(path):
         return None
-    src = open(os.path.join(ROOT, "paper_2108_13410_gb300", "csrc", "kernels.cuh"), "rb").read()
-    h = hashlib.sha256(src).hexdigest()[:16]
+    h = kernel_source_hash()
     vals = {}
     for line in open(path):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernels_cuh_sha256_16") != h:
+    if vals.get("kernel_source_sha256_16") != h:
         return None
     try:
         return float(vals["traffic_bytes_per_launch"])
@@ -265,8 +272,8 @@ def run_ours(args):
     achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
     peak, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profile_traffic("k_xpass_c64_27q"),
-                "kernel": "k_xpass<float>", "launches": xpass_n, "avg_launch_ms": avg_ms,
+                "frac": achieved / peak, "traffic": profile_traffic("k_xpass_tma_c64_27q"),
+                "kernel": "k_xpass_tma<2>", "launches": xpass_n, "avg_launch_ms": avg_ms,
                 "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
                 "step_hbm_gbs": (xpass_n / K) * alg_bytes / (ms / K / 1000.0) / 1e9}
 
@@ -342,7 +349,11 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pergate", action="store_true")
+    ap.add_argument("--source-hash", action="store_true", help="print the X-pass kernel source hash")
     args = ap.parse_args()
+    if args.source_hash:
+        print(kernel_source_hash())
+        return 0
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -363,7 +363,12 @@ __device__ __forceinline__ void block_store(double (&acc)[NVAL], double *out) {
     }
 }
 
-// values: [norm, sum_p <B_p>-weighted count sum (nA - 2 oddA), (nB - 2 oddB), Z-mask]
+// values: [norm, sum_i p_i (nA - 2 oddA(i)), sum_i p_i (nB - 2 oddB(i)), <Z_zmask>],
+// p_i = |psi_i|^2.  Products are summed in the state's precision over runs of
+// RED_RUN amplitudes (exact enough: 8 terms of one sign-pattern), and the runs are
+// accumulated in FP64.
+constexpr int RED_RUN = 8;
+
 template <typename R>
 __global__ void __launch_bounds__(RED_THREADS) k_reduce_diag(
     const typename C2<R>::T *__restrict__ psi, int n, long long state_stride,
@@ -375,16 +380,25 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_diag(
     __syncthreads();
     const int nbytes = (n + 7) / 8;
     const long long dim = 1ll << n;
+    const long long stride = (long long)gridDim.x * blockDim.x;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dim;
-         i += (long long)gridDim.x * blockDim.x) {
-        auto a = psi[i];
-        double p = (double)a.x * (double)a.x + (double)a.y * (double)a.y;
-        uint2 par = parity_of(tab, i, nbytes);
-        acc[0] += p;
-        acc[1] += p * (double)(nA - 2 * __popc(par.x));
-        acc[2] += p * (double)(nB - 2 * __popc(par.y));
-        acc[3] += (__popcll((unsigned long long)i & zmask) & 1) ? -p : p;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < dim; i0 += stride * RED_RUN) {
+        R f[4] = {0, 0, 0, 0};
+#pragma unroll
+        for (int u = 0; u < RED_RUN; ++u) {
+            long long i = i0 + u * stride;
+            if (i < dim) {
+                auto a = psi[i];
+                R p = a.x * a.x + a.y * a.y;
+                uint2 par = parity_of(tab, i, nbytes);
+                f[0] += p;
+                f[1] += p * (R)(nA - 2 * __popc(par.x));
+                f[2] += p * (R)(nB - 2 * __popc(par.y));
+                f[3] += (__popcll((unsigned long long)i & zmask) & 1) ? -p : p;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] += (double)f[v];
     }
     block_store<4>(acc, partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * RED_NV);
 }
@@ -397,13 +411,22 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_xmask(
     a += (long long)blockIdx.y * state_stride;
     b += (long long)blockIdx.y * state_stride;
     const long long dim = 1ll << n;
+    const long long stride = (long long)gridDim.x * blockDim.x;
     double acc[2] = {0.0, 0.0};
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dim;
-         i += (long long)gridDim.x * blockDim.x) {
-        auto x = a[i];
-        auto y = b[i ^ (long long)mask];
-        acc[0] += (double)x.x * (double)y.x + (double)x.y * (double)y.y;
-        acc[1] += (double)x.x * (double)y.y - (double)x.y * (double)y.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < dim; i0 += stride * RED_RUN) {
+        R f0 = 0, f1 = 0;
+#pragma unroll
+        for (int u = 0; u < RED_RUN; ++u) {
+            long long i = i0 + u * stride;
+            if (i < dim) {
+                auto x = a[i];
+                auto y = b[i ^ (long long)mask];
+                f0 += x.x * y.x + x.y * y.y;
+                f1 += x.x * y.y - x.y * y.x;
+            }
+        }
+        acc[0] += (double)f0;
+        acc[1] += (double)f1;
     }
     block_store<2>(acc, partials + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * RED_NV);
 }
