@@ -142,6 +142,22 @@ qs_status qs_expect_pauli(qs_sim *sim, int type, uint64_t mask, double *out);
  * state (same dtype, batch and size). out: host [batch]. */
 qs_status qs_fidelity(qs_sim *sim, const void *ref_dev_state, double *out);
 
+/* Reverse-mode gradient of a scalar of the final state with respect to the
+ * schedule.  Runs n_steps Trotter steps from the currently bound state psi_0 (as
+ * qs_evolve with the fused kernels), evaluates the value V (target 0: the final
+ * energy <psi_N|H1|psi_N>; target 1: the fidelity |<phi|psi_N>|^2 with phi =
+ * ref_dev_state, same layout as the bound state), then walks the Trotter factors in
+ * reverse, uncomputing psi and propagating lambda = dV/d<psi_N| with inverse
+ * factors (no stored intermediate states), and accumulates in FP64
+ *     dV/dtheta = 2 Re <lambda| i P |psi>
+ * for every factor exp(i theta P) of Eq. (8), chained to dV/ds_k.
+ * Outputs (host): dV_ds[b * n_steps + k], value_out[b].  On return slot 0 holds the
+ * reconstructed psi_0 (up to rounding) and slot 1 (which must be bound) is
+ * overwritten.  Gauge-Higgs form, at least 12 qubits.  Synchronises the stream. */
+qs_status qs_adjoint_grad(qs_sim *sim, const qs_couplings *couplings, const double *s, double dt,
+                          int n_steps, int order, int target, const void *ref_dev_state,
+                          double *dV_ds, double *value_out);
+
 /* Synchronise the bound stream and report device-side failures: QS_ERR_CUDA for
  * a failed launch, QS_ERR_TIMEOUT if a bounded wait inside a kernel gave up. */
 qs_status qs_sync(qs_sim *sim);

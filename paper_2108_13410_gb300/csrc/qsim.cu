@@ -18,6 +18,7 @@
 #include "lattice.h"
 #include "kernels.cuh"
 #include "xpass_tma.cuh"
+#include "adjoint.cuh"
 
 using namespace qsim;
 
@@ -80,6 +81,11 @@ struct qs_sim {
     std::vector<CUtensorMap> tmaps;        // one per pass, encoded for the bound state
     bool tmaps_ok = false;
     int *d_err = nullptr;                  // device flag: bounded wait gave up
+    // adjoint workspaces
+    double *d_adj_part = nullptr; size_t adj_part_cap = 0;
+    double *d_grad = nullptr; size_t grad_cap = 0;
+    double *h_grad = nullptr; size_t h_grad_cap = 0;
+    double *d_hrec = nullptr; size_t hrec_cap = 0;
 };
 
 #define FAIL(sim, code, ...)                                   \
@@ -614,6 +620,117 @@ qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_un
     return QS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// adjoint gradient
+// ---------------------------------------------------------------------------
+template <typename T>
+qs_status grow(qs_sim *s, T **p, size_t *cap, size_t need, bool host) {
+    if (need <= *cap) return QS_OK;
+    if (*p) {
+        if (host) cudaFreeHost(*p);
+        else { CK(s, cudaStreamSynchronize(s->stream)); cudaFree(*p); }
+    }
+    *p = nullptr; *cap = 0;
+    cudaError_t e = host ? cudaMallocHost((void **)p, need * sizeof(T)) : cudaMalloc((void **)p, need * sizeof(T));
+    if (e != cudaSuccess) FAIL(s, QS_ERR_OOM, "workspace of %zu elements", need);
+    *cap = need;
+    return QS_OK;
+}
+
+template <typename R>
+qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, double dt, int n_steps, int order,
+                       int target, const void *ref, double *grad_out, double *value_out) {
+    qs_status st;
+    const int B = s->batch;
+    const int np = (int)s->passes.size();
+    const long long ntiles = 1ll << (s->n - LT);
+    // ---- forward (fused kernels, no renormalisation) ----
+    const int saved_method = s->method, saved_renorm = s->renorm_every;
+    s->method = 0; s->renorm_every = 0;
+    std::vector<Op> ops = build_ops(c, B, sv, dt, n_steps, order, true);
+    st = run_ops<R>(s, ops, 1);
+    s->method = saved_method; s->renorm_every = saved_renorm;
+    if (st != QS_OK) return st;
+    const size_t nops = ops.size() / B;
+    V<R> *psi = (V<R> *)s->state[0];
+    V<R> *lam = (V<R> *)s->state[1];
+    const size_t smem = 2 * (size_t)(1 << LT) * sizeof(V<R>) + (size_t)(s->nA + 1) * (s->nB + 1) * sizeof(V<R>);
+    const unsigned G = (unsigned)std::min<long long>(ntiles, (long long)s->sm_count * 2);
+    // ---- seed lambda ----
+    if (target == 0) {
+        if ((st = grow(s, &s->d_hrec, &s->hrec_cap, (size_t)B * s->rec_stride, false)) != QS_OK) return st;
+        std::vector<double> h((size_t)B * s->rec_stride, 0.0);
+        for (int b = 0; b < B; ++b) {
+            double *r = &h[(size_t)b * s->rec_stride];
+            Coef q = coefficients(c[b], 1.0);          // H1
+            r[0] = -q.xs; r[2] = -q.xt;
+            for (int a = 0; a <= s->nA; ++a)
+                for (int bb = 0; bb <= s->nB; ++bb)
+                    r[4 + 2 * (a * (s->nB + 1) + bb)] = -(q.za * (s->nA - 2 * a) + q.zb * (s->nB - 2 * bb));
+        }
+        CK(s, cudaMemcpyAsync(s->d_hrec, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        for (int p = 0; p < np; ++p) {
+            k_apply_h_pass<R><<<dim3(G, B), NT, smem, s->stream>>>(psi, lam, s->dim, ntiles, s->d_hrec, s->rec_stride,
+                                                                  s->d_passes + 2 * p, p == 0);
+            CKL(s); s->launches++;
+        }
+        CK(s, cudaStreamSynchronize(s->stream));   // h is a host temporary
+        if ((st = reduce_xmask<R>(s, psi, lam, 0, 0)) != QS_OK) return st;   // <psi|H1|psi>
+    } else {
+        if (!ref) FAIL(s, QS_ERR_ARG, "fidelity target needs a reference state");
+        if ((st = reduce_xmask<R>(s, ref, psi, 0, 0)) != QS_OK) return st;   // <phi|psi>
+        k_scaled_copy<R><<<dim3(152 * 8, B), 256, 0, s->stream>>>(lam, (const V<R> *)ref, s->dim, s->d_res);
+        CKL(s); s->launches++;
+    }
+    if ((st = read_results(s, 1)) != QS_OK) return st;
+    for (int b = 0; b < B; ++b) {
+        double re = res(s, 0, b, 0), im = res(s, 0, b, 1);
+        value_out[b] = target == 0 ? re : re * re + im * im;
+    }
+    // ---- reverse sweep ----
+    const size_t nblk = (size_t)np * G;
+    if ((st = grow(s, &s->d_adj_part, &s->adj_part_cap, nblk * B * RED_NV, false)) != QS_OK) return st;
+    if ((st = grow(s, &s->d_grad, &s->grad_cap, nops * B * RED_NV, false)) != QS_OK) return st;
+    if ((st = grow(s, &s->h_grad, &s->h_grad_cap, nops * B * RED_NV, true)) != QS_OK) return st;
+    for (size_t jj = nops; jj-- > 0;) {
+        const double *rec = s->d_rec + jj * B * (size_t)s->rec_stride;
+        for (int pi = 0; pi < np; ++pi) {
+            const int p = np - 1 - pi;
+            k_adj_xpass<R><<<dim3(G, B), NT, smem, s->stream>>>(psi, lam, s->dim, ntiles, rec, s->rec_stride,
+                                                               s->d_passes + 2 * p, (pi == 0 && ops[jj * B].has_z) ? 1 : 0,
+                                                               s->d_adj_part, (int)nblk, pi * (int)G);
+            CKL(s); s->launches++;
+        }
+        k_finish<<<B, RED_THREADS, 0, s->stream>>>(s->d_adj_part, (int)nblk, 4, s->d_grad + jj * B * RED_NV);
+        CKL(s); s->launches++;
+    }
+    CK(s, cudaMemcpyAsync(s->h_grad, s->d_grad, nops * B * RED_NV * sizeof(double), cudaMemcpyDeviceToHost,
+                          s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    if ((st = check_device_flag(s)) != QS_OK) return st;
+    // ---- chain rule to s_k: dV/dtheta = -2 Im<lambda|P|psi> ----
+    const int N = n_steps;
+    for (int b = 0; b < B; ++b) {
+        double *g = grad_out + (size_t)b * N;
+        for (int k = 0; k < N; ++k) g[k] = 0.0;
+        const double dxs = c[b].g - 1.0, dxt = c[b].J - 1.0;   // d/ds of the X coefficients
+        for (size_t j = 0; j < nops; ++j) {
+            const double *v = s->h_grad + (j * B + b) * RED_NV;
+            for (int q = 0; q < 4; ++q)
+                if (!std::isfinite(v[q])) FAIL(s, QS_ERR_NONFINITE, "non-finite adjoint reduction");
+            const double gx = -2.0 * (dxs * v[0] + dxt * v[1]);
+            if (order == 1) {
+                g[j] += gx * dt;
+            } else {
+                if (j < (size_t)N) g[j] += gx * 0.5 * dt;
+                if (j >= 1) g[j - 1] += gx * 0.5 * dt;
+            }
+            if (ops[j * B].has_z) g[j] += -2.0 * (c[b].h * dt * v[2] + c[b].lambda * dt * v[3]);
+        }
+    }
+    return QS_OK;
+}
+
 qs_status check_ready(qs_sim *s) {
     if (!s) return QS_ERR_ARG;
     if (!s->state[0]) FAIL(s, QS_ERR_STATE, "no state bound (qs_bind_state slot 0)");
@@ -705,6 +822,11 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
                              (int)tma_smem_bytes(s, 2, true));
         cudaFuncSetAttribute(k_xpass_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tma_smem_bytes(s, 3, true));
+        int adj64 = (int)(2 * (1 << LT) * 16 + (size_t)(s->nA + 1) * (s->nB + 1) * 16);
+        cudaFuncSetAttribute(k_adj_xpass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
+        cudaFuncSetAttribute(k_adj_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
+        cudaFuncSetAttribute(k_apply_h_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
+        cudaFuncSetAttribute(k_apply_h_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
     }
     size_t smem64 = (size_t)(1 << LT) * 16 + (size_t)(s->nA + 1) * (s->nB + 1) * 16;
     cudaFuncSetAttribute(k_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
@@ -723,6 +845,10 @@ void qs_destroy(qs_sim *s) {
     cudaFree(s->d_partials);
     cudaFree(s->d_res);
     cudaFree(s->d_err);
+    cudaFree(s->d_adj_part);
+    cudaFree(s->d_grad);
+    cudaFree(s->d_hrec);
+    if (s->h_grad) cudaFreeHost(s->h_grad);
     if (s->h_rec) cudaFreeHost(s->h_rec);
     if (s->h_res) cudaFreeHost(s->h_res);
     if (s->rec_done) cudaEventDestroy(s->rec_done);
@@ -955,6 +1081,22 @@ qs_status qs_fidelity(qs_sim *s, const void *ref, double *out) {
         out[b] = re * re + im * im;
     }
     return QS_OK;
+}
+
+qs_status qs_adjoint_grad(qs_sim *s, const qs_couplings *c, const double *sv, double dt, int n_steps, int order,
+                          int target, const void *ref, double *dV_ds, double *value_out) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (!c || !sv || !dV_ds || !value_out) FAIL(s, QS_ERR_ARG, "null argument");
+    if (!s->state[1]) FAIL(s, QS_ERR_STATE, "the adjoint needs a work state bound to slot 1");
+    if (!s->lat.gauge_higgs) FAIL(s, QS_ERR_ARG, "the adjoint gradient supports the gauge-Higgs form");
+    if (s->n < LT) FAIL(s, QS_ERR_ARG, "the adjoint gradient needs at least %d qubits", LT);
+    if (order != 1 && order != 2) FAIL(s, QS_ERR_ARG, "order must be 1 or 2");
+    if (n_steps < 1) FAIL(s, QS_ERR_ARG, "n_steps must be >= 1");
+    if (target != 0 && target != 1) FAIL(s, QS_ERR_ARG, "target must be 0 (energy) or 1 (fidelity)");
+    if (s->dtype == QS_C64)
+        return adjoint_impl<float>(s, c, sv, dt, n_steps, order, target, ref, dV_ds, value_out);
+    return adjoint_impl<double>(s, c, sv, dt, n_steps, order, target, ref, dV_ds, value_out);
 }
 
 qs_status qs_sync(qs_sim *s) {

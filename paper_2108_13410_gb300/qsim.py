@@ -64,6 +64,7 @@ _SIGS = {
     "qs_expect_pauli": ([_P, _I, _U64, _DP], _I),
     "qs_fidelity": ([_P, _P, _DP], _I),
     "qs_sync": ([_P], _I),
+    "qs_adjoint_grad": ([_P, _CP, _DP, _D, _I, _I, _I, _P, _DP, _DP], _I),
     "qs_profile_read": ([_P, _DP, ctypes.POINTER(_LL)], _I),
     "qs_launch_count": ([_P], _LL),
     "qs_expect_z_noalloc": ([_P, _I, _I, _I, _U64, _P, _P], _I),
@@ -197,6 +198,18 @@ def qs_fidelity(sim, ref_dev_ptr: int, batch: int = 1):
     return out
 
 
+def qs_adjoint_grad(sim, couplings, s: Sequence[float], dt: float, order: int, target: int = 0,
+                    ref_dev_ptr: int | None = None, batch: int = 1):
+    """Returns (value[batch], dV/ds[batch, n_steps]) (see include/qsim.h)."""
+    arr = _couplings(couplings, batch)
+    sv = np.ascontiguousarray(s, dtype=np.float64)
+    grad = np.zeros((batch, sv.size), dtype=np.float64)
+    val = np.zeros(batch, dtype=np.float64)
+    _check(sim, library().qs_adjoint_grad(sim, arr, sv.ctypes.data_as(_DP), dt, int(sv.size), order, target,
+                                          ref_dev_ptr, grad.ctypes.data_as(_DP), val.ctypes.data_as(_DP)))
+    return val, grad
+
+
 def qs_sync(sim):
     _check(sim, library().qs_sync(sim))
 
@@ -313,6 +326,18 @@ class Simulator:
 
     def sync(self):
         qs_sync(self.h)
+
+    def adjoint_grad(self, couplings, s, dt, order=2, target="energy", ref_state=None):
+        """Forward evolution from the current state, value and dV/ds_k by the adjoint
+        sweep.  Needs aux=True at construction (the adjoint work state)."""
+        if self.aux is None:
+            raise ValueError("construct the Simulator with aux=True for the adjoint")
+        ref = None
+        if target == "fidelity":
+            assert ref_state is not None and ref_state.shape == self.state.shape
+            ref = ref_state.data_ptr()
+        return qs_adjoint_grad(self.h, couplings, s, dt, order, 0 if target == "energy" else 1, ref,
+                               self.batch)
 
     def profile_read(self):
         return qs_profile_read(self.h)

@@ -1,0 +1,119 @@
+"""Adjoint gradient (qs_adjoint_grad) against the oracle's forward-mode tangents and
+against central finite differences of the GPU evolution.
+
+Tolerances: complex128 gradients agree with the FP64 oracle to 1e-8 relative to the
+largest component; complex64 to 1e-3 relative (the complex64 amplitudes carry ~1e-6
+relative error, and each dV/ds_k sums many products of them).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import OracleLattice, Couplings
+from oracle import core as O
+
+gpu = pytest.mark.gpu
+
+
+def _sim(*a, **k):
+    from paper_2108_13410_gb300 import Simulator
+    return Simulator(*a, **k)
+
+
+def _close(got, ref, rel):
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= rel * scale + 1e-12, (np.max(np.abs(got - ref)), scale)
+
+
+def _tol(dtype):
+    return 1e-8 if dtype == "c128" else 1e-3
+
+
+@gpu
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("order", [1, 2])
+@pytest.mark.parametrize("lattice", [(2, 2), (3, 2)])
+def test_energy_gradient_matches_oracle(dtype, order, lattice):
+    Lx, Ly = lattice
+    lat = OracleLattice(Lx, Ly, True, "gh")
+    c = Couplings(0.6, 0.6)
+    T, n = 2.0, 16
+    a = synth.fourier_coeffs(4, seed=7, std=0.05)
+    s = O.schedule_fourier(T, n, a)
+    # dE/ds_k for every k: tangents seeded with the identity
+    e_ref, g_ref = O.energy_gradient(lat, c, s, T / n, order, np.eye(n))
+    sim = _sim(Lx, Ly, form="gh", dtype=dtype, aux=True)
+    sim.init_plus()
+    val, g = sim.adjoint_grad([(0.6, 0.6)], s, T / n, order)
+    assert abs(val[0] - e_ref) <= (1e-9 if dtype == "c128" else 1e-4 * abs(e_ref))
+    _close(g[0], g_ref, _tol(dtype))
+    # psi is uncomputed back to |+>
+    psi0 = sim.download()[0].numpy().astype(np.complex128)
+    drift = np.linalg.norm(psi0 - O.plus_state(lat.n_qubits))
+    assert drift <= (1e-11 if dtype == "c128" else 1e-4)
+
+
+@gpu
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_fidelity_gradient_matches_oracle(dtype):
+    import torch
+    lat = OracleLattice(3, 2, True, "gh")
+    c = Couplings(0.9, 0.4)
+    T, n, M = 2.0, 12, 3
+    a = synth.fourier_coeffs(M, seed=8, std=0.05)
+    s = O.schedule_fourier(T, n, a)
+    jac = O.schedule_fourier_jacobian(T, n, M)
+    phi = synth.random_state(lat.n_qubits, seed=31)
+    f_ref, gf_ref = O.fidelity_gradient(lat, c, s, T / n, 2, jac, phi)
+    sim = _sim(3, 2, form="gh", dtype=dtype, aux=True)
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    phi_dev = torch.from_numpy(phi.reshape(1, -1)).to(tdt).cuda()
+    sim.init_plus()
+    val, g = sim.adjoint_grad([(0.9, 0.4)], s, T / n, 2, target="fidelity", ref_state=phi_dev)
+    assert abs(val[0] - f_ref) <= (1e-12 if dtype == "c128" else 1e-6)
+    _close(jac @ g[0], gf_ref, _tol(dtype))
+
+
+@gpu
+def test_batched_adjoint_is_per_element():
+    couplings = [(0.2, 0.2), (0.6, 0.6)]
+    T, n = 2.0, 10
+    s = O.schedule_linear(T, n)
+    sim = _sim(2, 2, form="gh", dtype="c128", batch=2, aux=True)
+    sim.init_plus()
+    val, g = sim.adjoint_grad(couplings, s, T / n, 2)
+    lat = OracleLattice(2, 2, True, "gh")
+    for b, (gg, lam) in enumerate(couplings):
+        e_ref, g_ref = O.energy_gradient(lat, Couplings(gg, lam), s, T / n, 2, np.eye(n))
+        assert abs(val[b] - e_ref) <= 1e-9
+        _close(g[b], g_ref, 1e-8)
+
+
+@gpu
+def test_adjoint_matches_finite_differences_on_the_gpu_path():
+    """Central differences (h = 1e-4) of the complex128 GPU energy in the Fourier
+    amplitudes a_m against the adjoint chained through the autograd Function."""
+    import torch
+    from paper_2108_13410_gb300.autograd import schedule_value, fourier_schedule
+    T, n, M = 2.0, 20, 4
+    a0 = synth.fourier_coeffs(M, seed=2108, std=0.01)
+    sim = _sim(3, 2, form="gh", dtype="c128", aux=True)
+    cpl = [(0.6, 0.6)]
+    a = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
+    e = schedule_value(a, sim, cpl, T, n)
+    e.backward()
+
+    def energy(av):
+        s, _ = fourier_schedule(av, T, n)
+        sim.init_plus()
+        sim.evolve(cpl, s, T / n, 2)
+        return sim.energy(cpl)[0]
+
+    h = 1e-4
+    fd = []
+    for m in range(M):
+        d = np.zeros(M)
+        d[m] = h
+        fd.append((energy(a0 + d) - energy(a0 - d)) / (2 * h))
+    fd = np.array(fd)
+    assert np.max(np.abs(a.grad.numpy() - fd)) <= 1e-6 * max(1.0, np.max(np.abs(fd)))
