@@ -316,6 +316,9 @@ def run_ours(args):
         del sp
         torch.cuda.empty_cache()
 
+    if rank == 0 and args.adjoint_steps > 0:
+        extra["adjoint"] = adjoint_leg(args.adjoint_steps, local, dev, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         r, cores, desc = oracle_sample(args.cpu_budget)
@@ -340,6 +343,53 @@ def run_ours(args):
     return 0
 
 
+def adjoint_leg(n_steps, local, dev, stream):
+    """Adjoint-gradient time / forward time on the 27-qubit lattice with the Fourier
+    schedule s(t) = t/T + sum_{m<=16} a_m sin(m pi t/T), a_m ~ N(0, 0.01^2) (seed 2108),
+    T = 20, second order; complex64 forward, FP64 reductions.  The complex64 gradient
+    dE/da_m is compared with the complex128 adjoint on the same GPU."""
+    import torch
+    import synth
+    from paper_2108_13410_gb300 import Simulator
+    from paper_2108_13410_gb300.autograd import fourier_schedule
+    W = WORKLOAD
+    T = W["T"]
+    dt = T / n_steps
+    a = synth.fourier_coeffs(16, seed=2108, std=0.01)
+    s, jac = fourier_schedule(a, T, n_steps)
+    cpl = [(W["g"], W["lam"])]
+    out = {"steps": n_steps, "M": 16, "T": T}
+    grads = {}
+    for dtype in ("c64", "c128"):
+        sim = Simulator(W["Lx"], W["Ly"], form=W["form"], dtype=dtype, device=f"cuda:{local}", aux=True)
+        sim.init_plus()
+        sim.evolve(cpl, s[:3], dt, 2)
+        torch.cuda.synchronize(dev)
+        sim.init_plus()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.evolve(cpl, s, dt, 2)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        fwd_ms = e0.elapsed_time(e1)
+        sim.init_plus()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        val, g = sim.adjoint_grad(cpl, s, dt, 2)
+        adj_ms = (time.perf_counter() - t0) * 1000.0
+        grads[dtype] = jac @ g[0]
+        out[dtype] = {"forward_ms": fwd_ms, "adjoint_ms": adj_ms, "adjoint_over_forward": adj_ms / fwd_ms,
+                      "energy": float(val[0])}
+        del sim
+        torch.cuda.empty_cache()
+    ref = grads["c128"]
+    out["c64_grad_max_abs_err_vs_c128"] = float(np.max(np.abs(grads["c64"] - ref)))
+    out["grad_max_abs_c128"] = float(np.max(np.abs(ref)))
+    out["adjoint_over_forward"] = out["c64"]["adjoint_over_forward"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -347,6 +397,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--adjoint-steps", type=int, default=500)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pergate", action="store_true")
     ap.add_argument("--source-hash", action="store_true", help="print the X-pass kernel source hash")
