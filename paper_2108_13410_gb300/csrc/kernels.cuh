@@ -39,11 +39,17 @@ struct PassDesc {
     int stage1_on;              // stage 1 has something to rotate
     unsigned rot_mask[3];       // per stage: register bits to rotate
     int reg_cls[3][RB];         // X class (0 link sigma^x, 1 vertex tau^x) per register bit
-    int apply_z;                // multiply by the Z-layer phase before the store
-    int nA, nB;                 // Z class sizes (table is (nA+1) x (nB+1))
-    uint32_t colA[MAXQ];        // per global qubit: plaquettes containing it (bit p)
-    uint32_t colB[MAXQ];        // per global qubit: bonds / sigma^z terms containing it
+    int apply_z;                // multiply by a diagonal phase table before the store
+    int nA, nB;                 // table dims (nA+1) x (nB+1): odd terms of the two classes
+    uint32_t colA[MAXQ];        // per global qubit: class-A terms containing it (bit p)
+    uint32_t colB[MAXQ];        // per global qubit: class-B terms containing it
+    int hadamard;               // butterflies (a + b, a - b) instead of rotations
+    int lut_off;                // offset (doubles) of the phase table in the operator record
+    double scale;               // factor applied with the phase (a power of two)
 };
+// Diagonal tables: Z layer -- class A = plaquettes B_p, class B = bonds (gauge-Higgs)
+// or sigma^z_l (unitary gauge).  In the Hadamard basis of the unitary-gauge X layer
+// -- class A = stars A_v, class B = single links (X_l becomes Z_l).
 
 // Operator record (doubles): [u_sigma, s_sigma, u_tau, s_tau, then (nA+1)(nB+1)
 //   phase pairs (u, s) of exp(i phi(nA_odd, nB_odd))], where exp(i t) = (1 - u) + i s,
@@ -82,9 +88,27 @@ __device__ __forceinline__ V cphase(V v, V p) {
 
 __device__ __forceinline__ int swz(int l) { return l ^ ((l >> 4) & 15); }
 
+// unnormalised Hadamard butterfly: (a, b) <- (a + b, a - b)
+template <typename V>
+__device__ __forceinline__ void hbfly(V &a, V &b) {
+    V t = a;
+    a.x = t.x + b.x; a.y = t.y + b.y;
+    b.x = t.x - b.x; b.y = t.y - b.y;
+}
+
 template <typename R, typename V>
 __device__ __forceinline__ void rotate_regs(V (&v)[NR], unsigned mask, const int (&cls)[RB],
-                                            R u0, R s0, R u1, R s1) {
+                                            R u0, R s0, R u1, R s1, bool had = false) {
+    if (had) {
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            if (!((mask >> k) & 1u)) continue;
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                if (!((r >> k) & 1)) hbfly(v[r], v[r | (1 << k)]);
+        }
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
         if (!((mask >> k) & 1u)) continue;
@@ -120,10 +144,12 @@ __global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ ps
 
     const R u0 = (R)rec[0], s0 = (R)rec[1], u1 = (R)rec[2], s1 = (R)rec[3];
     const int apply_z = d->apply_z;
+    const bool had = d->hadamard != 0;
     const int nB1 = d->nB + 1;
     if (apply_z) {
         const int nl = (d->nA + 1) * nB1;
-        for (int i = t; i < nl; i += NT) lut[i] = mk<R>((R)rec[4 + 2 * i], (R)rec[5 + 2 * i]);
+        const double *tab = rec + d->lut_off;
+        for (int i = t; i < nl; i += NT) lut[i] = mk<R>((R)tab[2 * i], (R)tab[2 * i + 1]);
     }
     int lm[LT];
 #pragma unroll
@@ -150,7 +176,7 @@ __global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ ps
         int cls[RB];
 #pragma unroll
         for (int k = 0; k < RB; ++k) cls[k] = d->reg_cls[0][k];
-        rotate_regs<R>(v, d->rot_mask[0], cls, u0, s0, u1, s1);
+        rotate_regs<R>(v, d->rot_mask[0], cls, u0, s0, u1, s1, had);
 #pragma unroll
         for (int r = 0; r < NR; ++r) tile[swz(t | (r << TB))] = v[r];
     }
@@ -162,7 +188,7 @@ __global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ ps
         int cls[RB];
 #pragma unroll
         for (int k = 0; k < RB; ++k) cls[k] = d->reg_cls[1][k];
-        rotate_regs<R>(v, d->rot_mask[1], cls, u0, s0, u1, s1);
+        rotate_regs<R>(v, d->rot_mask[1], cls, u0, s0, u1, s1, had);
 #pragma unroll
         for (int r = 0; r < NR; ++r) tile[swz(r | (t << RB))] = v[r];
         __syncthreads();
@@ -175,7 +201,7 @@ __global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ ps
         int cls[RB];
 #pragma unroll
         for (int k = 0; k < RB; ++k) cls[k] = d->reg_cls[2][k];
-        rotate_regs<R>(v, d->rot_mask[2], cls, u0, s0, u1, s1);
+        rotate_regs<R>(v, d->rot_mask[2], cls, u0, s0, u1, s1, had);
     }
     long long toff = base;
 #pragma unroll
@@ -206,6 +232,11 @@ __global__ void __launch_bounds__(NT) k_xpass(typename C2<R>::T *__restrict__ ps
             for (int k = 0; k < RB; ++k)
                 if ((r >> k) & 1) { a ^= ra[k]; b ^= rb[k]; }
             v[r] = cphase(v[r], lut[__popc(a) * nB1 + __popc(b)]);
+        }
+        if (d->scale != 1.0) {
+            const R sc = (R)d->scale;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) { v[r].x *= sc; v[r].y *= sc; }
         }
     }
 #pragma unroll

@@ -38,6 +38,9 @@ struct Op {
 
 struct Coef { double xs, xt, za, zb; };
 
+// Pass variants: butterfly kind x diagonal phase applied before the store.
+enum { V_ROT = 0, V_ROT_Z = 1, V_HAD = 2, V_HAD_Z = 3, V_HAD_X = 4, NVAR = 5 };
+
 inline Coef coefficients(const qs_couplings &c, double s) {
     // -H(s) = sum coef * term, H(s) = (1-s) H0 + s H1
     return Coef{(1.0 - s) + s * c.g, (1.0 - s) + s * c.J, s * c.h, s * c.lambda};
@@ -61,8 +64,11 @@ struct qs_sim {
     std::string err;
     // tables
     int nA = 0, nB = 0, rec_stride = 0;
-    std::vector<PassDesc> passes;          // host copies (apply_z = 0)
-    PassDesc *d_passes = nullptr;          // device: [2 * pass + apply_z]
+    int nXA = 0, nXB = 0, xlut_off = 0;    // Hadamard-basis X table (unitary gauge)
+    int max_lut = 0;                       // largest phase table (entries)
+    std::vector<PassDesc> passes;          // pass plan (Z columns, no phase)
+    std::vector<PassDesc> pvar;            // [NVAR * pass + variant]
+    PassDesc *d_passes = nullptr;          // device copy of pvar
     uint32_t *d_colA = nullptr, *d_colB = nullptr;
     // operator records
     double *d_rec = nullptr; size_t d_rec_cap = 0;
@@ -77,7 +83,7 @@ struct qs_sim {
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
     int nbuf = 2;                          // TMA shared-memory buffers per CTA (2 or 3)
     int sm_count = 0;
-    std::vector<TmaPass> tpasses;          // [2 * pass + apply_z]
+    std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
     std::vector<CUtensorMap> tmaps;        // one per pass, encoded for the bound state
     bool tmaps_ok = false;
     int *d_err = nullptr;                  // device flag: bounded wait gave up
@@ -165,12 +171,41 @@ void build_passes(qs_sim *s) {
     }
 }
 
-// TMA pass descriptors derived from the pass plan (local bit j < c is global j;
+// Variants of every pass: rotation or Hadamard butterflies, and which diagonal
+// table (none, Z layer, or the Hadamard-basis X layer of the unitary gauge) is
+// applied before the store.
+void build_variants(qs_sim *s) {
+    s->pvar.clear();
+    uint32_t xa[64] = {0}, xb[64] = {0};
+    if (!s->lat.gauge_higgs)
+        for (int q = 0; q < s->n; ++q) {
+            for (size_t v = 0; v < s->lat.stars.size(); ++v)
+                if ((s->lat.stars[v] >> q) & 1) xa[q] |= 1u << v;
+            xb[q] = 1u << q;                 // every unitary-gauge qubit is a link
+        }
+    for (const PassDesc &d : s->passes)
+        for (int v = 0; v < NVAR; ++v) {
+            PassDesc e = d;
+            e.hadamard = v >= V_HAD;
+            e.apply_z = (v == V_ROT_Z || v == V_HAD_Z || v == V_HAD_X);
+            e.lut_off = 4;
+            e.scale = 1.0;
+            if (v == V_HAD_X) {
+                for (int q = 0; q < MAXQ; ++q) { e.colA[q] = q < 64 ? xa[q] : 0; e.colB[q] = q < 64 ? xb[q] : 0; }
+                e.nA = s->nXA; e.nB = s->nXB;
+                e.lut_off = s->xlut_off;
+                e.scale = ldexp(1.0, -s->n);   // two unnormalised transforms give 2^n
+            }
+            s->pvar.push_back(e);
+        }
+}
+
+// TMA pass descriptors derived from the pass variants (local bit j < c is global j;
 // local bit j >= c is global next + j - c).
 void build_tma_passes(qs_sim *s) {
     s->tpasses.clear();
     const int n = s->n;
-    for (const PassDesc &d : s->passes) {
+    for (const PassDesc &d : s->pvar) {
         int c = 0;
         while (c < LT && d.lmap[c] == c) ++c;
         const bool first = (c == LT);
@@ -204,16 +239,17 @@ void build_tma_passes(qs_sim *s) {
             P.rot[st] = d.rot_mask[st];
         }
         P.stage_b = P.rot[1] != 0;
-        P.nA = s->nA; P.nB = s->nB;
+        P.nA = d.nA; P.nB = d.nB;
+        P.apply_z = d.apply_z;
+        P.hadamard = d.hadamard;
+        P.lut_off = d.lut_off;
+        P.scale = (float)d.scale;
         P.tile_bits = n - LT;
         for (int i = 0; i < P.tile_bits && i < 32; ++i) {
             int q = i < P.mid_bits ? P.c + i : P.next + P.k + (i - P.mid_bits);
             P.pa_tile[i] = d.colA[q]; P.pb_tile[i] = d.colB[q];
         }
-        TmaPass Z = P; Z.apply_z = 1;
-        P.apply_z = 0;
         s->tpasses.push_back(P);
-        s->tpasses.push_back(Z);
     }
 }
 
@@ -235,7 +271,7 @@ qs_status encode_tmaps(qs_sim *s) {
     }
     const int n = s->n;
     for (size_t p = 0; p < s->passes.size(); ++p) {
-        const TmaPass &P = s->tpasses[2 * p];
+        const TmaPass &P = s->tpasses[NVAR * p];
         cuuint64_t dims[5] = {16, 1ull << (P.c - 4), 1ull << (P.next - P.c), 1ull << P.k,
                               (1ull << (n - P.next - P.k)) * (cuuint64_t)s->batch};
         cuuint64_t strides[4] = {16 * 8, (1ull << P.c) * 8, (1ull << P.next) * 8, (1ull << (P.next + P.k)) * 8};
@@ -254,7 +290,7 @@ qs_status encode_tmaps(qs_sim *s) {
 
 size_t tma_smem_bytes(const qs_sim *s, int nbuf, bool z) {
     size_t b = (size_t)nbuf * TMA_TILE_BYTES + 1024;
-    if (z) b += (size_t)(s->nA + 1) * (s->nB + 1) * 8 + 3 * 256 * 8;
+    if (z) b += (size_t)s->max_lut * 8 + 3 * 256 * 8;
     return b;
 }
 
@@ -303,6 +339,19 @@ void fill_record(const qs_sim *s, const Op &op, double *r) {
             double phi = op.zA * (double)(nA - 2 * a) + op.zB * (double)(nB - 2 * b);
             int e = a * (nB + 1) + b;
             unit_pair(f32, phi, &r[4 + 2 * e], &r[5 + 2 * e]);
+        }
+}
+
+// Hadamard-basis table of the unitary-gauge X layer: with a odd stars and b set link
+// bits, exp(i [theta_tau (nXA - 2a) + theta_sigma (nXB - 2b)]).
+void fill_xtable(const qs_sim *s, const Op &op, double *r) {
+    const bool f32 = s->dtype == QS_C64;
+    const int nA = s->nXA, nB = s->nXB;
+    for (int a = 0; a <= nA; ++a)
+        for (int b = 0; b <= nB; ++b) {
+            double phi = op.thx[1] * (double)(nA - 2 * a) + op.thx[0] * (double)(nB - 2 * b);
+            int e = a * (nB + 1) + b;
+            unit_pair(f32, phi, &r[s->xlut_off + 2 * e], &r[s->xlut_off + 2 * e + 1]);
         }
 }
 
@@ -358,10 +407,11 @@ template <typename R>
 using V = typename C2<R>::T;
 
 template <typename R>
-qs_status launch_xpass(qs_sim *s, int p, bool apply_z, const double *rec) {
-    const PassDesc &d = s->passes[p];
+qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec) {
+    const PassDesc &d = s->pvar[NVAR * p + variant];
+    const bool apply_z = d.apply_z != 0;
     dim3 grid((unsigned)(1ll << d.nfixed), (unsigned)s->batch);
-    size_t smem = (size_t)(1 << LT) * sizeof(V<R>) + (size_t)(s->nA + 1) * (s->nB + 1) * sizeof(V<R>);
+    size_t smem = (size_t)(1 << LT) * sizeof(V<R>) + (size_t)s->max_lut * sizeof(V<R>);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (s->profile) {
         while (s->ev_pool.size() < s->ev_used + 2) {
@@ -375,7 +425,7 @@ qs_status launch_xpass(qs_sim *s, int p, bool apply_z, const double *rec) {
     }
     const bool tma = sizeof(R) == 4 && s->tmaps_ok && s->xpass_impl != 1;
     if (tma) {
-        const TmaPass &P = s->tpasses[2 * p + (apply_z ? 1 : 0)];
+        const TmaPass &P = s->tpasses[NVAR * p + variant];
         size_t sm = tma_smem_bytes(s, s->nbuf, apply_z);
         int per_sm = 0;
         if (s->nbuf == 3)
@@ -392,7 +442,7 @@ qs_status launch_xpass(qs_sim *s, int p, bool apply_z, const double *rec) {
                                                                1ll << (s->n - LT), s->d_err, s->tmaps[p], P);
     } else {
         k_xpass<R><<<grid, NT, smem, s->stream>>>((V<R> *)s->state[0], s->dim, rec, s->rec_stride,
-                                                   s->d_passes + 2 * p + (apply_z ? 1 : 0));
+                                                   s->d_passes + NVAR * p + variant);
     }
     CKL(s);
     s->launches++;
@@ -435,11 +485,22 @@ qs_status run_op_fused(qs_sim *s, const Op *ops_b, const double *drec) {
                 CKL(s); s->launches++;
             }
         }
-    } else {
+    } else if (!ug) {
         for (int p = 0; p < np; ++p) {
-            bool z_here = has_z && !ug && p == np - 1;
-            if ((st = launch_xpass<R>(s, p, z_here, drec)) != QS_OK) return st;
+            bool z_here = has_z && p == np - 1;
+            if ((st = launch_xpass<R>(s, p, z_here ? V_ROT_Z : V_ROT, drec)) != QS_OK) return st;
         }
+        return QS_OK;
+    } else {
+        // unitary gauge: the X layer (sigma^x and A_v) is diagonal in the Hadamard
+        // basis: WHT, Hadamard-basis phase, WHT back (with the Z layer before the store)
+        for (int p = 0; p < np; ++p)
+            if ((st = launch_xpass<R>(s, p, p == np - 1 ? V_HAD_X : V_HAD, drec)) != QS_OK) return st;
+        for (int p = 0; p < np; ++p) {
+            bool z_here = has_z && p == np - 1;
+            if ((st = launch_xpass<R>(s, p, z_here ? V_HAD_Z : V_HAD, drec)) != QS_OK) return st;
+        }
+        return QS_OK;
     }
     if (ug) {
         for (int b = 0; b < s->batch; ++b) {
@@ -588,7 +649,10 @@ qs_status upload_records(qs_sim *s, const std::vector<Op> &ops) {
         // kernels queued earlier may still read d_rec: order the copy after them
     }
     memset(s->h_rec, 0, need * sizeof(double));
-    for (size_t i = 0; i < ops.size(); ++i) fill_record(s, ops[i], s->h_rec + i * s->rec_stride);
+    for (size_t i = 0; i < ops.size(); ++i) {
+        fill_record(s, ops[i], s->h_rec + i * s->rec_stride);
+        if (!s->lat.gauge_higgs) fill_xtable(s, ops[i], s->h_rec + i * s->rec_stride);
+    }
     CK(s, cudaMemcpyAsync(s->d_rec, s->h_rec, need * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CK(s, cudaEventRecord(s->rec_done, s->stream));
     s->rec_pending = true;
@@ -671,7 +735,7 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
         CK(s, cudaMemcpyAsync(s->d_hrec, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream));
         for (int p = 0; p < np; ++p) {
             k_apply_h_pass<R><<<dim3(G, B), NT, smem, s->stream>>>(psi, lam, s->dim, ntiles, s->d_hrec, s->rec_stride,
-                                                                  s->d_passes + 2 * p, p == 0);
+                                                                  s->d_passes + NVAR * p, p == 0);
             CKL(s); s->launches++;
         }
         CK(s, cudaStreamSynchronize(s->stream));   // h is a host temporary
@@ -697,7 +761,7 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
         for (int pi = 0; pi < np; ++pi) {
             const int p = np - 1 - pi;
             k_adj_xpass<R><<<dim3(G, B), NT, smem, s->stream>>>(psi, lam, s->dim, ntiles, rec, s->rec_stride,
-                                                               s->d_passes + 2 * p, (pi == 0 && ops[jj * B].has_z) ? 1 : 0,
+                                                               s->d_passes + NVAR * p, (pi == 0 && ops[jj * B].has_z) ? 1 : 0,
                                                                s->d_adj_part, (int)nblk, pi * (int)G);
             CKL(s); s->launches++;
         }
@@ -779,18 +843,24 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
     s->nB = (int)s->lat.second.size();
     if (s->nA > 32 || s->nB > 32) { g_create_error = "more than 32 terms in a Z class"; delete s; return QS_ERR_ARG; }
     s->rec_stride = record_doubles(s->nA, s->nB);
+    s->max_lut = (s->nA + 1) * (s->nB + 1);
+    if (!s->lat.gauge_higgs) {
+        s->nXA = (int)s->lat.stars.size();
+        s->nXB = s->lat.n_links;
+        if (s->nXA > 32 || s->nXB > 32) { g_create_error = "more than 32 terms in an X class"; delete s; return QS_ERR_ARG; }
+        s->xlut_off = s->rec_stride;
+        s->rec_stride += 2 * (s->nXA + 1) * (s->nXB + 1);
+        s->max_lut = std::max(s->max_lut, (s->nXA + 1) * (s->nXB + 1));
+    }
     build_passes(s);
+    build_variants(s);
     build_tma_passes(s);
     auto fail = [&](const char *what) {
         g_create_error = what;
         qs_destroy(s);
         return QS_ERR_OOM;
     };
-    std::vector<PassDesc> dev;
-    for (auto &d : s->passes) {
-        PassDesc a = d; a.apply_z = 0; dev.push_back(a);
-        PassDesc b = d; b.apply_z = 1; dev.push_back(b);
-    }
+    const std::vector<PassDesc> &dev = s->pvar;
     if (!dev.empty()) {
         if (cudaMalloc((void **)&s->d_passes, dev.size() * sizeof(PassDesc)) != cudaSuccess) return fail("pass table");
         if (cudaMemcpy(s->d_passes, dev.data(), dev.size() * sizeof(PassDesc), cudaMemcpyHostToDevice) != cudaSuccess)
@@ -828,7 +898,7 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
         cudaFuncSetAttribute(k_apply_h_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_apply_h_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
     }
-    size_t smem64 = (size_t)(1 << LT) * 16 + (size_t)(s->nA + 1) * (s->nB + 1) * 16;
+    size_t smem64 = (size_t)(1 << LT) * 16 + (size_t)s->max_lut * 16;
     cudaFuncSetAttribute(k_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
     cudaFuncSetAttribute(k_xpass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
     *out = s;

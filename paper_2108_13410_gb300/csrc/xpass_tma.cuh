@@ -42,6 +42,9 @@ struct TmaPass {
     uint32_t pa_reg[NR], pb_reg[NR];  // parity of stage-C register r
     uint32_t pa_tile[32], pb_tile[32];// parity columns of tile-index bits (bit order of tau)
     int tile_bits;              // tile-index bits that carry parity (not batch)
+    int hadamard;               // butterflies (a + b, a - b) instead of rotations
+    int lut_off;                // offset (doubles) of the phase table in the operator record
+    float scale;                // factor applied with the phase (a power of two)
 };
 
 constexpr int TMA_TILE_BYTES = (1 << LT) * 8;
@@ -177,7 +180,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             const double *rec = recs + batch * rec_stride;
             u0 = (float)rec[0]; s0 = (float)rec[1]; u1 = (float)rec[2]; s1 = (float)rec[3];
             if (P.apply_z)
-                for (int i = t; i < nlut; i += NT) lut[i] = make_float2((float)rec[4 + 2 * i], (float)rec[5 + 2 * i]);
+                for (int i = t; i < nlut; i += NT)
+                    lut[i] = make_float2((float)rec[P.lut_off + 2 * i], (float)rec[P.lut_off + 2 * i + 1]);
             cur_batch = batch;
         }
         if (t == 0) {
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             int cls[RB];
 #pragma unroll
             for (int kk = 0; kk < RB; ++kk) cls[kk] = (P.cls[0] >> kk) & 1;
-            rotate_regs<float>(v, P.rot[0], cls, u0, s0, u1, s1);
+            rotate_regs<float>(v, P.rot[0], cls, u0, s0, u1, s1, P.hadamard != 0);
         }
 #pragma unroll
         for (int r = 0; r < NR; ++r) tb[swz128(t | (r << TB))] = v[r];
@@ -219,7 +223,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             int cls[RB];
 #pragma unroll
             for (int kk = 0; kk < RB; ++kk) cls[kk] = (P.cls[1] >> kk) & 1;
-            rotate_regs<float>(v, P.rot[1], cls, u0, s0, u1, s1);
+            rotate_regs<float>(v, P.rot[1], cls, u0, s0, u1, s1, P.hadamard != 0);
 #pragma unroll
             for (int m = 0; m < NR / 2; ++m)
                 tb4[swz128((2 * m) | (t << RB)) >> 1] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x,
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             int cls[RB];
 #pragma unroll
             for (int kk = 0; kk < RB; ++kk) cls[kk] = (P.cls[2] >> kk) & 1;
-            rotate_regs<float>(v, P.rot[2], cls, u0, s0, u1, s1);
+            rotate_regs<float>(v, P.rot[2], cls, u0, s0, u1, s1, P.hadamard != 0);
         }
         // global base of the tile: mid bits -> global c.., upper bits (and batch) -> next+k..
         const long long tib = tile;
@@ -248,6 +252,10 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
 #pragma unroll
             for (int r = 0; r < NR; ++r)
                 v[r] = cphase(v[r], lut[__popc(pa ^ P.pa_reg[r]) * nB1 + __popc(pb ^ P.pb_reg[r])]);
+            if (P.scale != 1.0f) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) { v[r].x *= P.scale; v[r].y *= P.scale; }
+            }
         }
         float2 *dst = psi + gbase + toff;
 #pragma unroll

@@ -268,3 +268,44 @@ def test_complex64_xpass_kernels_agree(impl, nbuf):
     for b, (g, lam) in enumerate(couplings):
         ref = O.evolve(lat, Couplings(g, lam), s, T / n, 2)
         _assert_amplitudes(got[b], ref, "c64")
+
+
+@gpu
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_unitary_gauge_4x4_32_qubits(dtype):
+    """4x4 torus in the unitary gauge: 32 link qubits (32 GB complex64, 64 GB complex128).
+    One first-order step from |+>: |+> is an eigenstate of every X-type term (sigma^x
+    and A_v, eigenvalue +1), so the X layer is the global phase exp(i(th_s N_l + th_t N_v))
+    and amplitude i ends as 2^{-n/2} exp(i(th_s N_l + th_t N_v)) exp(i phi_Z(i)).
+    Then further second-order steps keep the norm, lattice symmetry and, at lambda = 0,
+    the 't Hooft loops."""
+    from paper_2108_13410_gb300 import QS_NORM, QS_PLAQUETTE, QS_THOOFT, QS_X
+    import torch
+    lat = OracleLattice(4, 4, True, "ug")
+    n = lat.n_qubits
+    g, lam, s, dt = 0.5, 0.0, 0.7, 0.05
+    sim = _sim(4, 4, form="ug", dtype=dtype)
+    sim.init_plus()
+    sim.trotter_step([(g, lam)], s, dt, 1)
+    coef = O.coefficients(Couplings(g, lam), s)
+    glob = coef["x_sigma"] * dt * 32 + coef["x_tau"] * dt * 16
+    rng = np.random.default_rng(9)
+    idx = rng.integers(0, 1 << n, 512)
+    amp = sim.state[0, torch.from_numpy(idx).to(sim.state.device)].cpu().numpy()
+    a = 2 ** (-n / 2)
+    for i, got in zip(idx, amp):
+        i = int(i)
+        ph = coef["z_plaq"] * sum(1 - 2 * (bin(i & m).count("1") & 1) for m in lat.z_plaquettes())
+        ph += coef["z_second"] * sum(1 - 2 * (bin(i & m).count("1") & 1) for m in lat.z_second())
+        want = a * np.exp(1j * (glob + dt * ph))
+        assert abs(got - want) <= _amp_tol(dtype) * a * 4
+    sim.evolve([(g, lam)], [0.2, 0.4, 0.6], 0.1, 2)
+    assert abs(sim.expect(QS_NORM)[0] - 1.0) <= (1e-10 if dtype == "c128" else 1e-5)
+    pl = [sim.expect(QS_PLAQUETTE, p)[0] for p in (0, 5, 15)]
+    assert max(pl) - min(pl) <= _obs_tol(dtype)
+    xs = [sim.expect(QS_X, q)[0] for q in (0, 17, 31)]
+    assert max(xs) - min(xs) <= _obs_tol(dtype)
+    for k in (0, 1):
+        assert abs(sim.expect(QS_THOOFT, k)[0] - 1.0) <= _obs_tol(dtype)
+    del sim
+    torch.cuda.empty_cache()
