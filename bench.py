@@ -288,9 +288,9 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(world, e2e_s, dev)
-    rec_bytes = (4 + 2 * 10 * 19) * 8                        # doubles per operator record (3x3)
     e2e = {"value": world * K / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": (state_bytes + (K + 1) * rec_bytes) / K,
+           # initial state + the schedule value of every step + one coupling record
+           "h2d_bytes_per_step": (state_bytes + 8 * K + 32) / K,
            "d2h_bytes_per_step": (1 + sim.n) * 4 * 8 / K,
            "final_energy": float(e_fin[0])}
 

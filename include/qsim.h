@@ -158,6 +158,22 @@ qs_status qs_adjoint_grad(qs_sim *sim, const qs_couplings *couplings, const doub
                           int n_steps, int order, int target, const void *ref_dev_state,
                           double *dV_ds, double *value_out);
 
+/* Observables returned per point by qs_scan. */
+#define QS_SCAN_NOBS 8
+
+/* Phase-diagram scan (Sec. V: energies along many parameter points).  Each of
+ * n_points coupling records is an independent run from |+>^n through the same
+ * schedule s[n_steps] (order 1 or 2, dt), with FP64 observables written to
+ * out[p * QS_SCAN_NOBS + k]: k = 0 <H1>, 1 average <B_p>, 2 <W_x>, 3 <W_y>
+ * (0 on open lattices), 4 norm, 5 average <sigma^x_l>, 6 average <tau^x_v>
+ * (0 in the unitary gauge), 7 reserved (0).
+ * A 12-qubit gauge-Higgs lattice (2x2 torus) runs every point in one persistent
+ * launch with the state in shared memory; sim needs no bound state.  Other
+ * lattices run in chunks of `batch` points through the tiled passes on the bound
+ * state (slot 0), which is overwritten.  Synchronises the stream. */
+qs_status qs_scan(qs_sim *sim, const qs_couplings *points, int n_points, const double *s, double dt,
+                  int n_steps, int order, double *out);
+
 /* Synchronise the bound stream and report device-side failures: QS_ERR_CUDA for
  * a failed launch, QS_ERR_TIMEOUT if a bounded wait inside a kernel gave up. */
 qs_status qs_sync(qs_sim *sim);

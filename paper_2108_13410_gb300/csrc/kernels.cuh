@@ -483,3 +483,102 @@ __global__ void k_finish(const double *__restrict__ partials, int nblk, int nval
 }
 
 }  // namespace qsim
+
+namespace qsim {
+
+// ---------------------------------------------------------------------------
+// Operator records built on the device from the schedule s[] and the couplings.
+// A record describes one Trotter factor group: X angles per class, then the Z
+// table (nA+1)(nB+1) and, for the unitary gauge, the Hadamard-basis X table.
+// Every exp(i t) is stored as (u, s) = (2 sin^2(t/2), sin t) computed in FP64; for
+// complex64 the float pair within +-3 ulps minimising |(1-u)^2 + s^2 - 1| is kept.
+// ---------------------------------------------------------------------------
+struct RecGeom {
+    int n_steps, order, fsal;    // fsal: second order with merged X half-steps
+    int batch, rec_stride;
+    int nA, nB, nXA, nXB, xlut_off;
+    int f32;
+    double dt;
+};
+
+struct DevCouplings { double J, h, g, lambda; };
+
+__device__ inline void dev_unit_pair(bool f32, double t, double *ou, double *os) {
+    double sh = sin(0.5 * t);
+    double u = 2.0 * sh * sh, s = sin(t);
+    if (!f32) { *ou = u; *os = s; return; }
+    float u0 = (float)u, s0 = (float)s, bu = u0, bs = s0;
+    double c0 = 1.0 - (double)u0;
+    double be = fabs(c0 * c0 + (double)s0 * (double)s0 - 1.0), bd = 0.0;
+    float uu = u0;
+    for (int i = 0; i < 3; ++i) uu = nextafterf(uu, -4.0f);
+    for (int i = -3; i <= 3; ++i, uu = nextafterf(uu, 4.0f)) {
+        float ss = s0;
+        for (int j = 0; j < 3; ++j) ss = nextafterf(ss, -4.0f);
+        for (int j = -3; j <= 3; ++j, ss = nextafterf(ss, 4.0f)) {
+            double c = 1.0 - (double)uu;
+            double e = fabs(c * c + (double)ss * (double)ss - 1.0);
+            double dd = fabs((double)uu - u) + fabs((double)ss - s);
+            if (e < be || (e == be && dd < bd)) { be = e; bd = dd; bu = uu; bs = ss; }
+        }
+    }
+    *ou = bu; *os = bs;
+}
+
+// X angles and Z angles of factor group `op` for couplings c:
+//   order 1:      op k (< N): X theta(s_k) dt, Z at s_k
+//   second order: op k (<= N): X theta(s_k) dt/2 [k < N] + theta(s_{k-1}) dt/2 [k > 0],
+//                 Z at s_k for k < N (the last group is the trailing X half-step)
+__device__ inline void dev_op_angles(const RecGeom &G, const DevCouplings &c, const double *__restrict__ sv,
+                                     int op, double *thx, double *zA, double *zB, bool *has_z) {
+    thx[0] = thx[1] = 0.0;
+    *zA = *zB = 0.0;
+    *has_z = false;
+    const int N = G.n_steps;
+    auto add = [&](int k, double tau) {
+        const double s = sv[k];
+        thx[0] += ((1.0 - s) + s * c.g) * tau;
+        thx[1] += ((1.0 - s) + s * c.J) * tau;
+    };
+    if (!G.fsal) {
+        add(op, G.dt);
+        *zA = sv[op] * c.h * G.dt; *zB = sv[op] * c.lambda * G.dt; *has_z = true;
+    } else {
+        if (op < N) add(op, 0.5 * G.dt);
+        if (op > 0) add(op - 1, 0.5 * G.dt);
+        if (op < N) { *zA = sv[op] * c.h * G.dt; *zB = sv[op] * c.lambda * G.dt; *has_z = true; }
+    }
+}
+
+// one thread per (op, batch, entry); entry 0 = X header, then Z table, then X table
+__global__ void k_build_records(RecGeom G, const DevCouplings *__restrict__ cpl, const double *__restrict__ sv,
+                                int n_ops, double *__restrict__ recs) {
+    const int nz = (G.nA + 1) * (G.nB + 1);
+    const int nx = G.xlut_off > 0 ? (G.nXA + 1) * (G.nXB + 1) : 0;
+    const long long per = 1 + nz + nx;
+    const long long total = (long long)n_ops * G.batch * per;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+         id += (long long)gridDim.x * blockDim.x) {
+        const long long ob = id / per;
+        const int e = (int)(id - ob * per);
+        const int op = (int)(ob / G.batch), b = (int)(ob % G.batch);
+        double thx[2], zA, zB;
+        bool has_z;
+        dev_op_angles(G, cpl[b], sv, op, thx, &zA, &zB, &has_z);
+        double *r = recs + ob * G.rec_stride;
+        if (e == 0) {
+            dev_unit_pair(G.f32, thx[0], &r[0], &r[1]);
+            dev_unit_pair(G.f32, thx[1], &r[2], &r[3]);
+        } else if (e <= nz) {
+            const int k = e - 1, a = k / (G.nB + 1), bb = k % (G.nB + 1);
+            double phi = has_z ? zA * (double)(G.nA - 2 * a) + zB * (double)(G.nB - 2 * bb) : 0.0;
+            dev_unit_pair(G.f32, phi, &r[4 + 2 * k], &r[5 + 2 * k]);
+        } else {
+            const int k = e - 1 - nz, a = k / (G.nXB + 1), bb = k % (G.nXB + 1);
+            double phi = thx[1] * (double)(G.nXA - 2 * a) + thx[0] * (double)(G.nXB - 2 * bb);
+            dev_unit_pair(G.f32, phi, &r[G.xlut_off + 2 * k], &r[G.xlut_off + 2 * k + 1]);
+        }
+    }
+}
+
+}  // namespace qsim

@@ -19,6 +19,7 @@
 #include "kernels.cuh"
 #include "xpass_tma.cuh"
 #include "adjoint.cuh"
+#include "scan.cuh"
 
 using namespace qsim;
 
@@ -92,6 +93,9 @@ struct qs_sim {
     double *d_grad = nullptr; size_t grad_cap = 0;
     double *h_grad = nullptr; size_t h_grad_cap = 0;
     double *d_hrec = nullptr; size_t hrec_cap = 0;
+    // scan workspaces
+    double *d_scan = nullptr; size_t scan_cap = 0;
+    double *h_scan = nullptr; size_t h_scan_cap = 0;
 };
 
 #define FAIL(sim, code, ...)                                   \
@@ -325,34 +329,6 @@ void unit_pair(bool f32, double t, double *ou, double *os) {
         }
     }
     *ou = bu; *os = bs;
-}
-
-void fill_record(const qs_sim *s, const Op &op, double *r) {
-    const bool f32 = s->dtype == QS_C64;
-    unit_pair(f32, op.thx[0], &r[0], &r[1]);
-    unit_pair(f32, op.thx[1], &r[2], &r[3]);
-    if (!op.has_z) return;
-    const int nA = s->nA, nB = s->nB;
-    for (int a = 0; a <= nA; ++a)
-        for (int b = 0; b <= nB; ++b) {
-            // exp(i [zA * sum_p (-1)^{pi_p} + zB * sum_b (-1)^{pi_b}]) with a odd plaquettes, b odd bonds
-            double phi = op.zA * (double)(nA - 2 * a) + op.zB * (double)(nB - 2 * b);
-            int e = a * (nB + 1) + b;
-            unit_pair(f32, phi, &r[4 + 2 * e], &r[5 + 2 * e]);
-        }
-}
-
-// Hadamard-basis table of the unitary-gauge X layer: with a odd stars and b set link
-// bits, exp(i [theta_tau (nXA - 2a) + theta_sigma (nXB - 2b)]).
-void fill_xtable(const qs_sim *s, const Op &op, double *r) {
-    const bool f32 = s->dtype == QS_C64;
-    const int nA = s->nXA, nB = s->nXB;
-    for (int a = 0; a <= nA; ++a)
-        for (int b = 0; b <= nB; ++b) {
-            double phi = op.thx[1] * (double)(nA - 2 * a) + op.thx[0] * (double)(nB - 2 * b);
-            int e = a * (nB + 1) + b;
-            unit_pair(f32, phi, &r[s->xlut_off + 2 * e], &r[s->xlut_off + 2 * e + 1]);
-        }
 }
 
 // ops[k * batch + b]
@@ -625,47 +601,68 @@ qs_status renormalise(qs_sim *s) {
     return QS_OK;
 }
 
-qs_status upload_records(qs_sim *s, const std::vector<Op> &ops) {
-    size_t need = ops.size() * (size_t)s->rec_stride;
+// Operator records for the fused path, built on the device by k_build_records from
+// the couplings and the schedule (the only host->device bytes per call).
+qs_status upload_records(qs_sim *s, size_t n_ops, const qs_couplings *c, const double *sv, double dt,
+                         int n_steps, int order) {
+    const int B = s->batch;
+    size_t need = n_ops * B * (size_t)s->rec_stride;
+    size_t in_doubles = (size_t)B * 4 + (size_t)n_steps;
     if (s->rec_pending) {
         CK(s, cudaEventSynchronize(s->rec_done));
         s->rec_pending = false;
     }
-    if (need > s->h_rec_cap) {
+    if (in_doubles > s->h_rec_cap) {
         if (s->h_rec) cudaFreeHost(s->h_rec);
         s->h_rec = nullptr;
-        if (cudaMallocHost((void **)&s->h_rec, need * sizeof(double)) != cudaSuccess)
-            FAIL(s, QS_ERR_OOM, "pinned record buffer (%zu doubles)", need);
-        s->h_rec_cap = need;
+        s->h_rec_cap = 0;
+        if (cudaMallocHost((void **)&s->h_rec, in_doubles * sizeof(double)) != cudaSuccess)
+            FAIL(s, QS_ERR_OOM, "pinned schedule buffer (%zu doubles)", in_doubles);
+        s->h_rec_cap = in_doubles;
     }
-    if (need > s->d_rec_cap) {
+    if (need + in_doubles > s->d_rec_cap) {
         // the previous device buffer may still be read by queued kernels
         if (s->d_rec) { CK(s, cudaStreamSynchronize(s->stream)); cudaFree(s->d_rec); }
         s->d_rec = nullptr;
-        if (cudaMalloc((void **)&s->d_rec, need * sizeof(double)) != cudaSuccess)
+        s->d_rec_cap = 0;
+        if (cudaMalloc((void **)&s->d_rec, (need + in_doubles) * sizeof(double)) != cudaSuccess)
             FAIL(s, QS_ERR_OOM, "device record buffer (%zu doubles)", need);
-        s->d_rec_cap = need;
-    } else {
-        // kernels queued earlier may still read d_rec: order the copy after them
+        s->d_rec_cap = need + in_doubles;
     }
-    memset(s->h_rec, 0, need * sizeof(double));
-    for (size_t i = 0; i < ops.size(); ++i) {
-        fill_record(s, ops[i], s->h_rec + i * s->rec_stride);
-        if (!s->lat.gauge_higgs) fill_xtable(s, ops[i], s->h_rec + i * s->rec_stride);
+    for (int b = 0; b < B; ++b) {
+        s->h_rec[4 * b + 0] = c[b].J; s->h_rec[4 * b + 1] = c[b].h;
+        s->h_rec[4 * b + 2] = c[b].g; s->h_rec[4 * b + 3] = c[b].lambda;
     }
-    CK(s, cudaMemcpyAsync(s->d_rec, s->h_rec, need * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    memcpy(s->h_rec + 4 * B, sv, (size_t)n_steps * sizeof(double));
+    double *d_in = s->d_rec + need;     // inputs live after the records
+    CK(s, cudaMemcpyAsync(d_in, s->h_rec, in_doubles * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CK(s, cudaEventRecord(s->rec_done, s->stream));
     s->rec_pending = true;
+    RecGeom G;
+    G.n_steps = n_steps; G.order = order; G.fsal = (order == 2);
+    G.batch = B; G.rec_stride = s->rec_stride;
+    G.nA = s->nA; G.nB = s->nB; G.nXA = s->nXA; G.nXB = s->nXB;
+    G.xlut_off = s->lat.gauge_higgs ? 0 : s->xlut_off;
+    G.f32 = s->dtype == QS_C64;
+    G.dt = dt;
+    long long entries = (long long)n_ops * B * (1 + (s->nA + 1) * (s->nB + 1) +
+                                               (G.xlut_off ? (s->nXA + 1) * (s->nXB + 1) : 0));
+    unsigned blocks = (unsigned)std::min<long long>((entries + 255) / 256, 152 * 16);
+    k_build_records<<<blocks, 256, 0, s->stream>>>(G, reinterpret_cast<const DevCouplings *>(d_in), d_in + 4 * B,
+                                                   (int)n_ops, s->d_rec);
+    CKL(s);
+    s->launches++;
     return QS_OK;
 }
 
 template <typename R>
-qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit) {
+qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit, const qs_couplings *c,
+                  const double *sv, double dt, int n_steps, int order) {
     qs_status st;
     const int B = s->batch;
     const size_t nops = ops.size() / B;
     if (s->method == 0) {
-        if ((st = upload_records(s, ops)) != QS_OK) return st;
+        if ((st = upload_records(s, nops, c, sv, dt, n_steps, order)) != QS_OK) return st;
         for (size_t k = 0; k < nops; ++k) {
             if ((st = run_op_fused<R>(s, &ops[k * B], s->d_rec + k * B * (size_t)s->rec_stride)) != QS_OK)
                 return st;
@@ -712,7 +709,7 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
     const int saved_method = s->method, saved_renorm = s->renorm_every;
     s->method = 0; s->renorm_every = 0;
     std::vector<Op> ops = build_ops(c, B, sv, dt, n_steps, order, true);
-    st = run_ops<R>(s, ops, 1);
+    st = run_ops<R>(s, ops, 1, c, sv, dt, n_steps, order);
     s->method = saved_method; s->renorm_every = saved_renorm;
     if (st != QS_OK) return st;
     const size_t nops = ops.size() / B;
@@ -918,6 +915,8 @@ void qs_destroy(qs_sim *s) {
     cudaFree(s->d_adj_part);
     cudaFree(s->d_grad);
     cudaFree(s->d_hrec);
+    cudaFree(s->d_scan);
+    if (s->h_scan) cudaFreeHost(s->h_scan);
     if (s->h_grad) cudaFreeHost(s->h_grad);
     if (s->h_rec) cudaFreeHost(s->h_rec);
     if (s->h_res) cudaFreeHost(s->h_res);
@@ -1019,8 +1018,8 @@ static qs_status evolve_impl(qs_sim *s, const qs_couplings *c, const double *sv,
     bool fsal = (s->method == 0);
     std::vector<Op> ops = build_ops(c, s->batch, sv, dt, n_steps, order, fsal);
     int per_step = (order == 2 && !fsal) ? 2 : 1;
-    if (s->dtype == QS_C64) return run_ops<float>(s, ops, per_step);
-    return run_ops<double>(s, ops, per_step);
+    if (s->dtype == QS_C64) return run_ops<float>(s, ops, per_step, c, sv, dt, n_steps, order);
+    return run_ops<double>(s, ops, per_step, c, sv, dt, n_steps, order);
 }
 
 qs_status qs_trotter_step(qs_sim *s, const qs_couplings *c, double sv, double dt, int order) {
@@ -1167,6 +1166,101 @@ qs_status qs_adjoint_grad(qs_sim *s, const qs_couplings *c, const double *sv, do
     if (s->dtype == QS_C64)
         return adjoint_impl<float>(s, c, sv, dt, n_steps, order, target, ref, dV_ds, value_out);
     return adjoint_impl<double>(s, c, sv, dt, n_steps, order, target, ref, dV_ds, value_out);
+}
+
+qs_status qs_scan(qs_sim *s, const qs_couplings *points, int n_points, const double *sv, double dt, int n_steps,
+                  int order, double *out) {
+    if (!s) return QS_ERR_ARG;
+    if (!points || !sv || !out) FAIL(s, QS_ERR_ARG, "null argument");
+    if (n_points < 1 || n_steps < 1) FAIL(s, QS_ERR_ARG, "n_points and n_steps must be >= 1");
+    if (order != 1 && order != 2) FAIL(s, QS_ERR_ARG, "order must be 1 or 2");
+    const int nops = order == 2 ? n_steps + 1 : n_steps;
+    if (s->n == LT && s->lat.gauge_higgs && (s->nA + 1) * (s->nB + 1) <= 64) {
+        // ---- every point in one persistent launch, state in shared memory ----
+        size_t in_doubles = (size_t)n_points * 4 + (size_t)n_steps;
+        size_t out_doubles = (size_t)n_points * SCAN_NOBS;
+        qs_status st;
+        if ((st = grow(s, &s->d_scan, &s->scan_cap, in_doubles + out_doubles, false)) != QS_OK) return st;
+        if ((st = grow(s, &s->h_scan, &s->h_scan_cap, in_doubles + out_doubles, true)) != QS_OK) return st;
+        for (int p = 0; p < n_points; ++p) {
+            s->h_scan[4 * p] = points[p].J; s->h_scan[4 * p + 1] = points[p].h;
+            s->h_scan[4 * p + 2] = points[p].g; s->h_scan[4 * p + 3] = points[p].lambda;
+        }
+        memcpy(s->h_scan + 4 * (size_t)n_points, sv, (size_t)n_steps * sizeof(double));
+        ScanParams P;
+        memset(&P, 0, sizeof(P));
+        P.n_points = n_points; P.n_ops = nops;
+        P.G.n_steps = n_steps; P.G.order = order; P.G.fsal = order == 2; P.G.batch = 1; P.G.dt = dt;
+        P.G.f32 = s->dtype == QS_C64;
+        P.nA = s->nA; P.nB = s->nB;
+        for (int q = 0; q < LT; ++q) {
+            for (int k = 0; k < s->nA; ++k) if ((s->lat.plaquettes[k] >> q) & 1) P.colA[q] |= 1u << k;
+            for (int k = 0; k < s->nB; ++k) if ((s->lat.second[k] >> q) & 1) P.colB[q] |= 1u << k;
+            if (s->lat.x_class[q]) P.cls_mask |= 1u << q;
+        }
+        if (s->lat.wilson.size() == 2) { P.wx = (uint32_t)s->lat.wilson[0]; P.wy = (uint32_t)s->lat.wilson[1]; }
+        P.n_link = s->lat.n_links; P.n_vertex = s->n - s->lat.n_links;
+        CK(s, cudaMemcpyAsync(s->d_scan, s->h_scan, in_doubles * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        int per_sm = 0;
+        if (s->dtype == QS_C64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan12<float>, NT, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan12<double>, NT, 0);
+        if (per_sm < 1) per_sm = 1;
+        unsigned grid = (unsigned)std::min<long long>(n_points, (long long)per_sm * s->sm_count);
+        const DevCouplings *dc = reinterpret_cast<const DevCouplings *>(s->d_scan);
+        double *dout = s->d_scan + in_doubles;
+        if (s->dtype == QS_C64)
+            k_scan12<float><<<grid, NT, 0, s->stream>>>(dc, s->d_scan + 4 * n_points, dout, P);
+        else
+            k_scan12<double><<<grid, NT, 0, s->stream>>>(dc, s->d_scan + 4 * n_points, dout, P);
+        CKL(s); s->launches++;
+        CK(s, cudaMemcpyAsync(s->h_scan + in_doubles, dout, out_doubles * sizeof(double), cudaMemcpyDeviceToHost,
+                              s->stream));
+        CK(s, cudaStreamSynchronize(s->stream));
+        memcpy(out, s->h_scan + in_doubles, out_doubles * sizeof(double));
+        return QS_OK;
+    }
+    // ---- larger lattices: chunks of `batch` points through the tiled passes ----
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    const int B = s->batch;
+    std::vector<qs_couplings> chunk(B);
+    std::vector<double> tmp(B);
+    for (int p0 = 0; p0 < n_points; p0 += B) {
+        const int cnt = std::min(B, n_points - p0);
+        for (int b = 0; b < B; ++b) chunk[b] = points[p0 + std::min(b, cnt - 1)];
+        if ((st = qs_init_plus(s)) != QS_OK) return st;
+        if ((st = qs_evolve(s, chunk.data(), sv, dt, n_steps, order)) != QS_OK) return st;
+        auto put = [&](int k, const double *v) {
+            for (int b = 0; b < cnt; ++b) out[(size_t)(p0 + b) * SCAN_NOBS + k] = v[b];
+        };
+        if ((st = qs_expect(s, QS_ENERGY, 0, chunk.data(), 1.0, tmp.data())) != QS_OK) return st;
+        put(0, tmp.data());
+        if ((st = qs_expect(s, QS_PLAQUETTE, -1, nullptr, 1.0, tmp.data())) != QS_OK) return st;
+        put(1, tmp.data());
+        for (int w = 0; w < 2; ++w) {
+            if (w < (int)s->lat.wilson.size()) {
+                if ((st = qs_expect(s, QS_WILSON, w, nullptr, 1.0, tmp.data())) != QS_OK) return st;
+            } else {
+                std::fill(tmp.begin(), tmp.end(), 0.0);
+            }
+            put(2 + w, tmp.data());
+        }
+        if ((st = qs_expect(s, QS_NORM, 0, nullptr, 1.0, tmp.data())) != QS_OK) return st;
+        put(4, tmp.data());
+        // link / vertex <X> averages
+        std::vector<double> xs(B, 0.0), xt(B, 0.0);
+        for (int q = 0; q < s->n; ++q) {
+            if ((st = qs_expect(s, QS_X, q, nullptr, 1.0, tmp.data())) != QS_OK) return st;
+            for (int b = 0; b < B; ++b) (s->lat.x_class[q] ? xt : xs)[b] += tmp[b];
+        }
+        const int nl = s->lat.n_links, nv = s->n - s->lat.n_links;
+        for (int b = 0; b < B; ++b) { xs[b] = nl ? xs[b] / nl : 0.0; xt[b] = nv ? xt[b] / nv : 0.0; }
+        put(5, xs.data());
+        put(6, xt.data());
+        std::fill(tmp.begin(), tmp.end(), 0.0);
+        put(7, tmp.data());
+    }
+    return QS_OK;
 }
 
 qs_status qs_sync(qs_sim *s) {

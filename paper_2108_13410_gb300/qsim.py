@@ -64,6 +64,7 @@ _SIGS = {
     "qs_expect_pauli": ([_P, _I, _U64, _DP], _I),
     "qs_fidelity": ([_P, _P, _DP], _I),
     "qs_sync": ([_P], _I),
+    "qs_scan": ([_P, _CP, _I, _DP, _D, _I, _I, _DP], _I),
     "qs_adjoint_grad": ([_P, _CP, _DP, _D, _I, _I, _I, _P, _DP, _DP], _I),
     "qs_profile_read": ([_P, _DP, ctypes.POINTER(_LL)], _I),
     "qs_launch_count": ([_P], _LL),
@@ -210,6 +211,19 @@ def qs_adjoint_grad(sim, couplings, s: Sequence[float], dt: float, order: int, t
     return val, grad
 
 
+QS_SCAN_NOBS = 8
+
+
+def qs_scan(sim, points, s: Sequence[float], dt: float, order: int = 2):
+    """Independent runs for every coupling record; returns out[n_points, QS_SCAN_NOBS]."""
+    pts = _couplings(points, len(points))
+    sv = np.ascontiguousarray(s, dtype=np.float64)
+    out = np.zeros((len(points), QS_SCAN_NOBS), dtype=np.float64)
+    _check(sim, library().qs_scan(sim, pts, len(points), sv.ctypes.data_as(_DP), dt, int(sv.size), order,
+                                  out.ctypes.data_as(_DP)))
+    return out
+
+
 def qs_sync(sim):
     _check(sim, library().qs_sync(sim))
 
@@ -326,6 +340,9 @@ class Simulator:
 
     def sync(self):
         qs_sync(self.h)
+
+    def scan(self, points, s, dt, order=2):
+        return qs_scan(self.h, points, s, dt, order)
 
     def adjoint_grad(self, couplings, s, dt, order=2, target="energy", ref_state=None):
         """Forward evolution from the current state, value and dV/ds_k by the adjoint
