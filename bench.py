@@ -316,6 +316,9 @@ def run_ours(args):
         del sp
         torch.cuda.empty_cache()
 
+    if rank == 0 and not args.no_scan:
+        extra["scan"] = scan_leg(local, dev)
+
     if rank == 0 and args.adjoint_steps > 0:
         extra["adjoint"] = adjoint_leg(args.adjoint_steps, local, dev, stream)
 
@@ -341,6 +344,43 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def scan_leg(local, dev, chunk=64):
+    """Phase-diagram scan: 1024 (g, lambda) points on a 32 x 32 grid of [0, 1.5]^2,
+    even flat index -> 2x2 periodic gauge-Higgs (12 qubits, one persistent launch),
+    odd -> 3x2 open unitary gauge (17 qubits, batched chunks); complex64, linear
+    ramp T = 10, 200 second-order steps."""
+    import torch
+    import synth
+    from paper_2108_13410_gb300 import Simulator
+    grid = synth.coupling_grid(32, 0.0, 1.5)
+    pts = [tuple(p) for p in grid]
+    even, odd = pts[0::2], pts[1::2]
+    T, n = 10.0, 200
+    s = linear_midpoints(T, n)
+    out = {"points": len(pts), "steps": n, "T": T}
+    sim12 = Simulator(2, 2, form="gh", dtype="c64", device=f"cuda:{local}")
+    sim12.scan(even[:8], s[:5], T / n, 2)                      # warm-up
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    r12 = sim12.scan(even, s, T / n, 2)
+    t12 = time.perf_counter() - t0
+    sim17 = Simulator(3, 2, form="ug", dtype="c64", boundary="open", batch=chunk, device=f"cuda:{local}")
+    sim17.scan(odd[:chunk], s[:5], T / n, 2)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    r17 = sim17.scan(odd, s, T / n, 2)
+    t17 = time.perf_counter() - t0
+    out["gh2x2_12q"] = {"points": len(even), "seconds": t12, "point_steps_per_s": len(even) * n / t12,
+                        "launches": 1, "energy_range": [float(r12[:, 0].min()), float(r12[:, 0].max())]}
+    out["ug3x2open_17q"] = {"points": len(odd), "seconds": t17, "point_steps_per_s": len(odd) * n / t17,
+                            "chunk": chunk, "energy_range": [float(r17[:, 0].min()), float(r17[:, 0].max())]}
+    out["seconds"] = t12 + t17
+    out["point_steps_per_s"] = len(pts) * n / (t12 + t17)
+    del sim12, sim17
+    torch.cuda.empty_cache()
+    return out
 
 
 def adjoint_leg(n_steps, local, dev, stream):
@@ -398,6 +438,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--adjoint-steps", type=int, default=500)
+    ap.add_argument("--no-scan", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pergate", action="store_true")
     ap.add_argument("--source-hash", action="store_true", help="print the X-pass kernel source hash")
