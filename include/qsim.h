@@ -178,6 +178,19 @@ qs_status qs_scan(qs_sim *sim, const qs_couplings *points, int n_points, const d
  * a failed launch, QS_ERR_TIMEOUT if a bounded wait inside a kernel gave up. */
 qs_status qs_sync(qs_sim *sim);
 
+/* Failure-detection self-test: launches a kernel that waits on an mbarrier which
+ * never completes, with the same bounded wait as the TMA X pass, limited to
+ * limit_ms (0 < limit_ms <= 2000).  Expected result: QS_ERR_TIMEOUT, with the
+ * context still usable afterwards. */
+qs_status qs_selftest_wait(qs_sim *sim, double limit_ms);
+
+/* Checkpoint: write (qs_save) or read (qs_load) the bound state with a header
+ * recording lattice, boundary, form, dtype, batch and size; qs_load rejects a file
+ * written for a different simulator.  Resuming with qs_evolve from a loaded state
+ * continues bit-identically.  Synchronise the stream. */
+qs_status qs_save(qs_sim *sim, const char *path);
+qs_status qs_load(qs_sim *sim, const char *path);
+
 /* Total milliseconds and launch count of the fused X-pass kernel since the last
  * read, when QS_OPT_PROFILE is on.  Synchronises the stream. */
 qs_status qs_profile_read(qs_sim *sim, double *total_ms, long long *launches);

@@ -93,6 +93,11 @@ struct qs_sim {
     double *d_grad = nullptr; size_t grad_cap = 0;
     double *h_grad = nullptr; size_t h_grad_cap = 0;
     double *d_hrec = nullptr; size_t hrec_cap = 0;
+    // CUDA graph of the last qs_evolve launch sequence (QS_OPT_GRAPH)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_key[10] = {0};
+    long long graph_launches = 0;
     // scan workspaces
     double *d_scan = nullptr; size_t scan_cap = 0;
     double *h_scan = nullptr; size_t h_scan_cap = 0;
@@ -656,28 +661,59 @@ qs_status upload_records(qs_sim *s, size_t n_ops, const qs_couplings *c, const d
 }
 
 template <typename R>
+qs_status launch_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit) {
+    qs_status st;
+    const int B = s->batch;
+    const size_t nops = ops.size() / B;
+    for (size_t k = 0; k < nops; ++k) {
+        if (s->method == 0)
+            st = run_op_fused<R>(s, &ops[k * B], s->d_rec + k * B * (size_t)s->rec_stride);
+        else
+            st = run_op_pergate<R>(s, &ops[k * B]);
+        if (st != QS_OK) return st;
+        if (s->renorm_every > 0 && steps_per_renorm_unit > 0 &&
+            ((k + 1) % ((size_t)s->renorm_every * steps_per_renorm_unit) == 0 || k + 1 == nops))
+            if ((st = renormalise<R>(s)) != QS_OK) return st;
+    }
+    return QS_OK;
+}
+
+template <typename R>
 qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit, const qs_couplings *c,
                   const double *sv, double dt, int n_steps, int order) {
     qs_status st;
     const int B = s->batch;
     const size_t nops = ops.size() / B;
-    if (s->method == 0) {
+    if (s->method == 0)
         if ((st = upload_records(s, nops, c, sv, dt, n_steps, order)) != QS_OK) return st;
-        for (size_t k = 0; k < nops; ++k) {
-            if ((st = run_op_fused<R>(s, &ops[k * B], s->d_rec + k * B * (size_t)s->rec_stride)) != QS_OK)
-                return st;
-            if (s->renorm_every > 0 && steps_per_renorm_unit > 0 &&
-                ((k + 1) % ((size_t)s->renorm_every * steps_per_renorm_unit) == 0 || k + 1 == nops))
-                if ((st = renormalise<R>(s)) != QS_OK) return st;
-        }
-    } else {
-        for (size_t k = 0; k < nops; ++k) {
-            if ((st = run_op_pergate<R>(s, &ops[k * B])) != QS_OK) return st;
-            if (s->renorm_every > 0 && steps_per_renorm_unit > 0 &&
-                ((k + 1) % ((size_t)s->renorm_every * steps_per_renorm_unit) == 0 || k + 1 == nops))
-                if ((st = renormalise<R>(s)) != QS_OK) return st;
-        }
+    if (!s->use_graph || s->profile) return launch_ops<R>(s, ops, steps_per_renorm_unit);
+    // Replay the launch sequence as a CUDA graph, captured once per configuration on a
+    // private stream; the records it reads are rebuilt in place before every replay.
+    const long long key[10] = {(long long)nops, order, n_steps, B, (long long)(uintptr_t)s->state[0],
+                               (long long)(uintptr_t)s->d_rec, s->renorm_every, s->xpass_impl * 16 + s->nbuf,
+                               s->method, (long long)s->dtype};
+    if (!s->graph_exec || memcmp(key, s->graph_key, sizeof(key)) != 0) {
+        if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
+        if (!s->cap_stream) CK(s, cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t user = s->stream;
+        s->stream = s->cap_stream;
+        long long before = s->launches;
+        CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+        st = launch_ops<R>(s, ops, steps_per_renorm_unit);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
+        s->stream = user;
+        s->graph_launches = s->launches - before;
+        s->launches = before;
+        if (st != QS_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) FAIL(s, QS_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&s->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) { s->graph_exec = nullptr; FAIL(s, QS_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+        memcpy(s->graph_key, key, sizeof(key));
     }
+    CK(s, cudaGraphLaunch(s->graph_exec, s->stream));
+    s->launches += s->graph_launches;
     return QS_OK;
 }
 
@@ -916,6 +952,8 @@ void qs_destroy(qs_sim *s) {
     cudaFree(s->d_grad);
     cudaFree(s->d_hrec);
     cudaFree(s->d_scan);
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->h_scan) cudaFreeHost(s->h_scan);
     if (s->h_grad) cudaFreeHost(s->h_grad);
     if (s->h_rec) cudaFreeHost(s->h_rec);
@@ -1261,6 +1299,81 @@ qs_status qs_scan(qs_sim *s, const qs_couplings *points, int n_points, const dou
         put(7, tmp.data());
     }
     return QS_OK;
+}
+
+qs_status qs_selftest_wait(qs_sim *s, double limit_ms) {
+    if (!s) return QS_ERR_ARG;
+    if (!(limit_ms > 0.0 && limit_ms <= 2000.0)) FAIL(s, QS_ERR_ARG, "limit_ms must be in (0, 2000]");
+    int dev = 0, khz = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+    if (khz <= 0) khz = 2000000;
+    long long cycles = (long long)(limit_ms * (double)khz);
+    k_wait_probe<<<1, 32, 0, s->stream>>>(s->d_err, cycles);
+    CKL(s); s->launches++;
+    CK(s, cudaStreamSynchronize(s->stream));
+    return check_device_flag(s);
+}
+
+// ---- checkpoint: header + raw state ----
+namespace {
+struct CkptHeader {
+    char magic[8];        // "QSIMCKP1"
+    int32_t Lx, Ly, boundary, form, dtype, batch, n;
+    int32_t reserved;
+    uint64_t state_bytes;
+};
+}
+
+qs_status qs_save(qs_sim *s, const char *path) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (!path) FAIL(s, QS_ERR_ARG, "null path");
+    const size_t bytes = qs_state_bytes(s);
+    void *host = nullptr;
+    if (cudaMallocHost(&host, bytes) != cudaSuccess) FAIL(s, QS_ERR_OOM, "pinned staging of %zu bytes", bytes);
+    st = qs_download_state(s, host, bytes);
+    if (st == QS_OK) {
+        FILE *f = fopen(path, "wb");
+        if (!f) { cudaFreeHost(host); FAIL(s, QS_ERR_ARG, "cannot open %s for writing", path); }
+        CkptHeader h;
+        memset(&h, 0, sizeof(h));
+        memcpy(h.magic, "QSIMCKP1", 8);
+        h.Lx = s->lat.Lx; h.Ly = s->lat.Ly; h.boundary = s->boundary; h.form = s->form;
+        h.dtype = s->dtype; h.batch = s->batch; h.n = s->n; h.state_bytes = bytes;
+        bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(host, 1, bytes, f) == bytes;
+        ok = (fclose(f) == 0) && ok;
+        if (!ok) { cudaFreeHost(host); FAIL(s, QS_ERR_ARG, "short write to %s", path); }
+    }
+    cudaFreeHost(host);
+    return st;
+}
+
+qs_status qs_load(qs_sim *s, const char *path) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (!path) FAIL(s, QS_ERR_ARG, "null path");
+    FILE *f = fopen(path, "rb");
+    if (!f) FAIL(s, QS_ERR_ARG, "cannot open %s", path);
+    CkptHeader h;
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, "QSIMCKP1", 8) != 0) {
+        fclose(f);
+        FAIL(s, QS_ERR_ARG, "%s is not a qsim checkpoint", path);
+    }
+    const size_t bytes = qs_state_bytes(s);
+    if (h.Lx != s->lat.Lx || h.Ly != s->lat.Ly || h.boundary != s->boundary || h.form != s->form ||
+        h.dtype != s->dtype || h.batch != s->batch || h.n != s->n || h.state_bytes != bytes) {
+        fclose(f);
+        FAIL(s, QS_ERR_ARG, "checkpoint %s was written for another lattice, dtype or batch", path);
+    }
+    void *host = nullptr;
+    if (cudaMallocHost(&host, bytes) != cudaSuccess) { fclose(f); FAIL(s, QS_ERR_OOM, "pinned staging"); }
+    bool ok = fread(host, 1, bytes, f) == bytes;
+    fclose(f);
+    if (!ok) { cudaFreeHost(host); FAIL(s, QS_ERR_ARG, "truncated checkpoint %s", path); }
+    st = qs_upload_state(s, host, bytes);
+    cudaFreeHost(host);
+    return st;
 }
 
 qs_status qs_sync(qs_sim *s) {

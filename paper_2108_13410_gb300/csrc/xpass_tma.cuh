@@ -264,3 +264,19 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
 }
 
 }  // namespace qsim
+
+namespace qsim {
+
+// Self-test of the bounded wait: an mbarrier that expects one arrival which never
+// comes.  mbar_wait_bounded gives up after max_cycles, the kernel records the
+// timeout in err_flag (bit 1) and returns; nothing faults and the context stays usable.
+__global__ void k_wait_probe(int *__restrict__ err_flag, long long max_cycles) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (!mbar_wait_bounded(&bar, 0, max_cycles)) atomicOr(err_flag, 2);
+    }
+}
+
+}  // namespace qsim

@@ -64,6 +64,9 @@ _SIGS = {
     "qs_expect_pauli": ([_P, _I, _U64, _DP], _I),
     "qs_fidelity": ([_P, _P, _DP], _I),
     "qs_sync": ([_P], _I),
+    "qs_selftest_wait": ([_P, _D], _I),
+    "qs_save": ([_P, ctypes.c_char_p], _I),
+    "qs_load": ([_P, ctypes.c_char_p], _I),
     "qs_scan": ([_P, _CP, _I, _DP, _D, _I, _I, _DP], _I),
     "qs_adjoint_grad": ([_P, _CP, _DP, _D, _I, _I, _I, _P, _DP, _DP], _I),
     "qs_profile_read": ([_P, _DP, ctypes.POINTER(_LL)], _I),
@@ -224,6 +227,18 @@ def qs_scan(sim, points, s: Sequence[float], dt: float, order: int = 2):
     return out
 
 
+def qs_selftest_wait(sim, limit_ms: float):
+    _check(sim, library().qs_selftest_wait(sim, float(limit_ms)))
+
+
+def qs_save(sim, path: str):
+    _check(sim, library().qs_save(sim, os.fsencode(path)))
+
+
+def qs_load(sim, path: str):
+    _check(sim, library().qs_load(sim, os.fsencode(path)))
+
+
 def qs_sync(sim):
     _check(sim, library().qs_sync(sim))
 
@@ -340,6 +355,12 @@ class Simulator:
 
     def sync(self):
         qs_sync(self.h)
+
+    def save(self, path):
+        qs_save(self.h, path)
+
+    def load(self, path):
+        qs_load(self.h, path)
 
     def scan(self, points, s, dt, order=2):
         return qs_scan(self.h, points, s, dt, order)

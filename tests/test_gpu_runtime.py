@@ -1,0 +1,104 @@
+"""Runtime features around the evolution: CUDA-graph replay, renormalisation,
+checkpoint/resume and the device-side bounded wait (failure detection)."""
+import numpy as np
+import pytest
+
+from oracle import OracleLattice, Couplings
+from oracle import core as O
+
+gpu = pytest.mark.gpu
+
+
+def _sim(*a, **k):
+    from paper_2108_13410_gb300 import Simulator
+    return Simulator(*a, **k)
+
+
+@gpu
+@pytest.mark.parametrize("form,L", [("gh", (3, 2)), ("ug", (2, 5))])
+def test_graph_replay_is_bit_identical(form, L):
+    from paper_2108_13410_gb300 import QS_OPT_GRAPH
+    T, n = 2.0, 12
+    s = O.schedule_linear(T, n)
+    a = _sim(*L, form=form, dtype="c64")
+    b = _sim(*L, form=form, dtype="c64")
+    b.set_option(QS_OPT_GRAPH, 1)
+    for sim in (a, b):
+        sim.init_plus()
+        sim.evolve([(0.6, 0.6)], s, T / n, 2)
+    assert np.array_equal(a.download().numpy(), b.download().numpy())
+    # replay with a different schedule of the same length reuses the graph
+    s2 = O.schedule_linear(2 * T, n)
+    for sim in (a, b):
+        sim.init_plus()
+        sim.evolve([(0.3, 0.9)], s2, T / n, 2)
+        sim.sync()
+    assert np.array_equal(a.download().numpy(), b.download().numpy())
+
+
+@gpu
+def test_renormalisation_keeps_unit_norm_and_the_state():
+    from paper_2108_13410_gb300 import QS_NORM
+    lat = OracleLattice(3, 2, True, "gh")
+    T, n = 4.0, 80
+    s = O.schedule_linear(T, n)
+    ref = O.evolve(lat, Couplings(0.6, 0.6), s, T / n, 2)
+    sim = _sim(3, 2, form="gh", dtype="c64", renorm_every=10)
+    sim.init_plus()
+    sim.evolve([(0.6, 0.6)], s, T / n, 2)
+    assert abs(sim.expect(QS_NORM)[0] - 1.0) <= 1e-6
+    got = sim.download()[0].numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) <= 1e-5
+
+
+@gpu
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_checkpoint_resume_is_bit_identical(tmp_path, dtype):
+    T, n = 2.0, 20
+    s = O.schedule_linear(T, n)
+    full = _sim(3, 2, form="gh", dtype=dtype)
+    full.init_plus()
+    full.evolve([(0.6, 0.6)], s, T / n, 1)
+    part = _sim(3, 2, form="gh", dtype=dtype)
+    part.init_plus()
+    part.evolve([(0.6, 0.6)], s[:9], T / n, 1)
+    path = str(tmp_path / "ckpt.qs")
+    part.save(path)
+    resumed = _sim(3, 2, form="gh", dtype=dtype)
+    resumed.load(path)
+    resumed.evolve([(0.6, 0.6)], s[9:], T / n, 1)
+    assert np.array_equal(full.download().numpy(), resumed.download().numpy())
+    other = _sim(2, 2, form="gh", dtype=dtype)
+    from paper_2108_13410_gb300 import QsError
+    with pytest.raises(QsError):
+        other.load(path)
+
+
+@gpu
+def test_bounded_wait_times_out_and_the_context_survives():
+    from paper_2108_13410_gb300 import QsError
+    from paper_2108_13410_gb300.qsim import qs_selftest_wait
+    sim = _sim(3, 2, form="gh", dtype="c64")
+    with pytest.raises(QsError) as e:
+        qs_selftest_wait(sim.h, 50.0)
+    assert e.value.status == 5                     # QS_ERR_TIMEOUT
+    # the context is still usable
+    lat = OracleLattice(3, 2, True, "gh")
+    s = O.schedule_linear(1.0, 5)
+    sim.init_plus()
+    sim.evolve([(0.6, 0.6)], s, 0.2, 2)
+    sim.sync()
+    ref = O.evolve(lat, Couplings(0.6, 0.6), s, 0.2, 2)
+    got = sim.download()[0].numpy().astype(np.complex128)
+    assert np.linalg.norm(got - ref) <= 1e-5
+
+
+@gpu
+def test_launch_count_is_reported():
+    sim = _sim(3, 3, form="gh", dtype="c64")
+    sim.init_plus()
+    sim.launch_count()
+    sim.evolve([(0.6, 0.6)], O.schedule_linear(1.0, 10), 0.1, 2)
+    sim.sync()
+    # device-built records (1) + 3 passes x 10 steps + 3 trailing passes
+    assert sim.launch_count() == 1 + 3 * 11
