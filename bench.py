@@ -146,6 +146,12 @@ def barrier(world):
         dist.barrier()
 
 
+def job_throughput(world: int, steps_per_rank: int, ms_max: float) -> float:
+    """Whole-job steps/s: every rank evolves its own replica for steps_per_rank steps;
+    the job takes as long as the slowest rank."""
+    return world * steps_per_rank / (ms_max / 1000.0)
+
+
 def max_over_ranks(world, x: float, device):
     if world == 1:
         return x
@@ -264,7 +270,7 @@ def run_ours(args):
     xpass_ms, xpass_n = sim.profile_read()
     sim.set_option(QS_OPT_PROFILE, 0)
     ms_max = max_over_ranks(world, ms, dev)
-    value = world * K / (ms_max / 1000.0)
+    value = job_throughput(world, K, ms_max)
 
     state_bytes = sim.state_bytes
     alg_bytes = 2.0 * state_bytes                     # one read + one write of the state per pass
