@@ -417,10 +417,10 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec) {
         long long g = std::min<long long>(P.total_tiles, (long long)per_sm * s->sm_count);
         if (s->nbuf == 3)
             k_xpass_tma<3><<<(unsigned)g, NT, sm, s->stream>>>((float2 *)s->state[0], rec, s->rec_stride,
-                                                               1ll << (s->n - LT), s->d_err, s->tmaps[p], P);
+                                                               s->n - LT, s->d_err, s->tmaps[p], P);
         else
             k_xpass_tma<2><<<(unsigned)g, NT, sm, s->stream>>>((float2 *)s->state[0], rec, s->rec_stride,
-                                                               1ll << (s->n - LT), s->d_err, s->tmaps[p], P);
+                                                               s->n - LT, s->d_err, s->tmaps[p], P);
     } else {
         k_xpass<R><<<grid, NT, smem, s->stream>>>((V<R> *)s->state[0], s->dim, rec, s->rec_stride,
                                                    s->d_passes + NVAR * p + variant);

@@ -95,7 +95,7 @@ __device__ __forceinline__ int swz128(int l) { return l ^ (((l >> 4) & 7) << 1);
 
 template <int NBUF>
 __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__restrict__ psi, const double *__restrict__ recs,
-                                                  int rec_stride, long long tiles_per_state,
+                                                  int rec_stride, int tiles_shift,
                                                   int *__restrict__ err_flag,
                                                   const __grid_constant__ CUtensorMap tmap,
                                                   const __grid_constant__ TmaPass P) {
@@ -150,13 +150,19 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         tma_load_5d(buf + (size_t)b * (1 << LT), &tmap, &bars[b], 0, x1, x2, 0, x4);
     };
 
-    long long n_my = (T - first + G - 1) / G;   // tiles this CTA processes
-    if (first >= T) n_my = 0;
+    const int n_my = first < T ? (int)((T - first + G - 1) / G) : 0;   // tiles this CTA processes
     if (t == 0)
-        for (long long it = 0; it < NBUF - 1 && it < n_my; ++it) issue(it);
+        for (int it = 0; it < NBUF - 1 && it < n_my; ++it) issue(it);
 
-    // per-thread constants of stage C
+    // per-thread constants: shared-memory bases of the three stages (the 128-byte
+    // swizzle touches amplitude bits 1..3 only, from bits 4..6), stage-C offsets
     const int tlo = t & 15, thi = t >> 4;
+    const int a_base = swz128(t);                     // stage A: + (r << 8)
+    int c_base[8];                                    // stage C: c_base[r & 7] + (r << 4)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c_base[j] = (tlo ^ (j << 1)) | (thi << 8);
+    const int b_base = t << 3;                        // stage B, float4 index
+    const int b_x = t & 7;                            // stage B swizzle of the float4 slot
     long long toff = 0;
     uint32_t pa_t = 0, pb_t = 0;
 #pragma unroll
@@ -166,16 +172,23 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
     }
     const int nB1 = P.nB + 1;
     const int nlut = (P.nA + 1) * nB1;
+    const bool had = P.hadamard != 0;
     long long cur_batch = -1;
     float u0 = 0.f, s0 = 0.f, u1 = 0.f, s1 = 0.f;
+    int cls0[RB], cls1[RB], cls2[RB];
+#pragma unroll
+    for (int kk = 0; kk < RB; ++kk) {
+        cls0[kk] = (P.cls[0] >> kk) & 1; cls1[kk] = (P.cls[1] >> kk) & 1; cls2[kk] = (P.cls[2] >> kk) & 1;
+    }
+    const long long tmask = (1ll << tiles_shift) - 1;
 
-    for (long long it = 0; it < n_my; ++it) {
-        const long long tile = first + it * G;
-        const int b = (int)(it % NBUF);
+    long long tile = first;
+    for (int it = 0; it < n_my; ++it, tile += G) {
+        const int b = it % NBUF;
         const uint32_t parity = (uint32_t)((it / NBUF) & 1);
-        const long long batch = tile / tiles_per_state;
+        const long long batch = tile >> tiles_shift;
         if (batch != cur_batch) {
-            // operator record of this batch element (angles, Z table)
+            // operator record of this batch element (angles, phase table)
             __syncthreads();
             const double *rec = recs + batch * rec_stride;
             u0 = (float)rec[0]; s0 = (float)rec[1]; u1 = (float)rec[2]; s1 = (float)rec[3];
@@ -189,7 +202,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                 atomicOr(err_flag, 1);
                 s_ok = 0;
                 // wait (bounded) for every load this CTA still has in flight before leaving
-                for (long long j = it; j < it + NBUF - 1 && j < n_my; ++j)
+                for (int j = it; j < it + NBUF - 1 && j < n_my; ++j)
                     mbar_wait_bounded(&bars[j % NBUF], (uint32_t)((j / NBUF) & 1), max_wait);
             }
         }
@@ -201,51 +214,53 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         float2 v[NR];
         // ---- stage A: registers = local 8..11 ----
 #pragma unroll
-        for (int r = 0; r < NR; ++r) v[r] = tb[swz128(t | (r << TB))];
-        {
-            int cls[RB];
+        for (int r = 0; r < NR; ++r) v[r] = tb[a_base + (r << TB)];
+        rotate_regs<float>(v, P.rot[0], cls0, u0, s0, u1, s1, had);
 #pragma unroll
-            for (int kk = 0; kk < RB; ++kk) cls[kk] = (P.cls[0] >> kk) & 1;
-            rotate_regs<float>(v, P.rot[0], cls, u0, s0, u1, s1, P.hadamard != 0);
-        }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) tb[swz128(t | (r << TB))] = v[r];
+        for (int r = 0; r < NR; ++r) tb[a_base + (r << TB)] = v[r];
         __syncthreads();
         // ---- stage B: registers = local 0..3 (16-byte accesses) ----
         if (P.stage_b) {
             float4 *tb4 = reinterpret_cast<float4 *>(tb);
+            if (!had) {
+                // A rotation butterfly is symmetric in its two amplitudes, so the
+                // thread may hold its eight float4 slots in physical order: slot j
+                // carries local bits 1..3 equal to j ^ (t & 7), and every pair of
+                // registers differing in one bit is still a pair of that qubit.
 #pragma unroll
-            for (int m = 0; m < NR / 2; ++m) {
-                float4 q = tb4[swz128((2 * m) | (t << RB)) >> 1];
-                v[2 * m] = make_float2(q.x, q.y);
-                v[2 * m + 1] = make_float2(q.z, q.w);
+                for (int m = 0; m < NR / 2; ++m) {
+                    float4 q = tb4[b_base + m];
+                    v[2 * m] = make_float2(q.x, q.y);
+                    v[2 * m + 1] = make_float2(q.z, q.w);
+                }
+                rotate_regs<float>(v, P.rot[1], cls1, u0, s0, u1, s1, false);
+#pragma unroll
+                for (int m = 0; m < NR / 2; ++m)
+                    tb4[b_base + m] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
+            } else {
+#pragma unroll
+                for (int m = 0; m < NR / 2; ++m) {
+                    float4 q = tb4[b_base + (m ^ b_x)];
+                    v[2 * m] = make_float2(q.x, q.y);
+                    v[2 * m + 1] = make_float2(q.z, q.w);
+                }
+                rotate_regs<float>(v, P.rot[1], cls1, u0, s0, u1, s1, true);
+#pragma unroll
+                for (int m = 0; m < NR / 2; ++m)
+                    tb4[b_base + (m ^ b_x)] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
             }
-            int cls[RB];
-#pragma unroll
-            for (int kk = 0; kk < RB; ++kk) cls[kk] = (P.cls[1] >> kk) & 1;
-            rotate_regs<float>(v, P.rot[1], cls, u0, s0, u1, s1, P.hadamard != 0);
-#pragma unroll
-            for (int m = 0; m < NR / 2; ++m)
-                tb4[swz128((2 * m) | (t << RB)) >> 1] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x,
-                                                                    v[2 * m + 1].y);
             __syncthreads();
         }
-        // ---- stage C: registers = local 4..7; Z layer; store ----
+        // ---- stage C: registers = local 4..7; diagonal phase; store ----
 #pragma unroll
-        for (int r = 0; r < NR; ++r) v[r] = tb[swz128(tlo | (r << 4) | (thi << 8))];
-        {
-            int cls[RB];
-#pragma unroll
-            for (int kk = 0; kk < RB; ++kk) cls[kk] = (P.cls[2] >> kk) & 1;
-            rotate_regs<float>(v, P.rot[2], cls, u0, s0, u1, s1, P.hadamard != 0);
-        }
+        for (int r = 0; r < NR; ++r) v[r] = tb[c_base[r & 7] + (r << 4)];
+        rotate_regs<float>(v, P.rot[2], cls2, u0, s0, u1, s1, had);
         // global base of the tile: mid bits -> global c.., upper bits (and batch) -> next+k..
-        const long long tib = tile;
-        const long long mid = tib & ((1ll << P.mid_bits) - 1);
-        const long long up = tib >> P.mid_bits;
+        const long long mid = tile & ((1ll << P.mid_bits) - 1);
+        const long long up = tile >> P.mid_bits;
         const long long gbase = (mid << P.c) + (up << (P.next + P.k));
         if (P.apply_z) {
-            const long long tin = tile - batch * tiles_per_state;   // parity ignores batch
+            const long long tin = tile & tmask;                       // parity ignores batch
             uint2 e0 = ptab[tin & 255], e1 = ptab[256 + ((tin >> 8) & 255)], e2 = ptab[512 + ((tin >> 16) & 255)];
             const uint32_t pa = pa_t ^ e0.x ^ e1.x ^ e2.x;
             const uint32_t pb = pb_t ^ e0.y ^ e1.y ^ e2.y;
