@@ -388,7 +388,7 @@ template <typename R>
 using V = typename C2<R>::T;
 
 template <typename R>
-qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec) {
+qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int frame = 0) {
     const PassDesc &d = s->pvar[NVAR * p + variant];
     const bool apply_z = d.apply_z != 0;
     dim3 grid((unsigned)(1ll << d.nfixed), (unsigned)s->batch);
@@ -406,7 +406,8 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec) {
     }
     const bool tma = sizeof(R) == 4 && s->tmaps_ok && s->xpass_impl != 1;
     if (tma) {
-        const TmaPass &P = s->tpasses[NVAR * p + variant];
+        TmaPass P = s->tpasses[NVAR * p + variant];
+        P.frame = frame;
         size_t sm = tma_smem_bytes(s, s->nbuf, apply_z);
         int per_sm = 0;
         if (s->nbuf == 3)
@@ -447,9 +448,11 @@ qs_status launch_zdiag(qs_sim *s, const double *rec) {
     return QS_OK;
 }
 
-// Apply ops[first .. first+count) (each a batch of records already on the device at drec).
+// Apply one factor group (records already on the device at drec); k / nops place
+// it in the current qs_evolve call (the TMA kernel keeps the state in the real-
+// rotation frame between the first and the last pass of the call).
 template <typename R>
-qs_status run_op_fused(qs_sim *s, const Op *ops_b, const double *drec) {
+qs_status run_op_fused(qs_sim *s, const Op *ops_b, const double *drec, size_t k = 0, size_t nops = 1) {
     qs_status st;
     const bool ug = !s->lat.gauge_higgs;
     const int np = (int)s->passes.size();
@@ -467,9 +470,12 @@ qs_status run_op_fused(qs_sim *s, const Op *ops_b, const double *drec) {
             }
         }
     } else if (!ug) {
+        const bool tma = sizeof(R) == 4 && s->tmaps_ok && s->xpass_impl != 1;
         for (int p = 0; p < np; ++p) {
             bool z_here = has_z && p == np - 1;
-            if ((st = launch_xpass<R>(s, p, z_here ? V_ROT_Z : V_ROT, drec)) != QS_OK) return st;
+            int frame = 0;
+            if (tma) frame = 1 | ((k == 0 && p == 0) ? 2 : 0) | ((k + 1 == nops && p == np - 1) ? 4 : 0);
+            if ((st = launch_xpass<R>(s, p, z_here ? V_ROT_Z : V_ROT, drec, frame)) != QS_OK) return st;
         }
         return QS_OK;
     } else {
@@ -667,7 +673,7 @@ qs_status launch_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm
     const size_t nops = ops.size() / B;
     for (size_t k = 0; k < nops; ++k) {
         if (s->method == 0)
-            st = run_op_fused<R>(s, &ops[k * B], s->d_rec + k * B * (size_t)s->rec_stride);
+            st = run_op_fused<R>(s, &ops[k * B], s->d_rec + k * B * (size_t)s->rec_stride, k, nops);
         else
             st = run_op_pergate<R>(s, &ops[k * B]);
         if (st != QS_OK) return st;

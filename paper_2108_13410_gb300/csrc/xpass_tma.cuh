@@ -45,6 +45,8 @@ struct TmaPass {
     int hadamard;               // butterflies (a + b, a - b) instead of rotations
     int lut_off;                // offset (doubles) of the phase table in the operator record
     float scale;                // factor applied with the phase (a power of two)
+    int frame;                  // bit 0: rotations in the frame phi_i = i^popc(i) psi_i;
+                                // bit 1: convert psi -> phi at stage A; bit 2: phi -> psi at stage C
 };
 
 constexpr int TMA_TILE_BYTES = (1 << LT) * 8;
@@ -92,6 +94,50 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, u
 }
 
 __device__ __forceinline__ int swz128(int l) { return l ^ (((l >> 4) & 7) << 1); }
+
+// packed FP32x2 fused multiply-add: (a.x * b.x + c.x, a.y * b.y + c.y)
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// In the frame phi_i = i^{popcount(i)} psi_i, exp(i theta X_q) becomes the real rotation
+// [[cos, sin], [-sin, cos]] (S X S^dagger = Y with S = diag(1, i)), which treats the real
+// and imaginary parts alike:  a' = a - u a + s b,  b' = b - u b - s a  (cos = 1 - u).
+__device__ __forceinline__ void rrot(float2 &a, float2 &b, float2 nu, float2 ps, float2 ns) {
+    const float2 ta = fma2(nu, a, a);
+    const float2 tb = fma2(nu, b, b);
+    const float2 na = fma2(ps, b, ta);
+    const float2 nb = fma2(ns, a, tb);
+    a = na;
+    b = nb;
+}
+
+__device__ __forceinline__ void rotate_regs_phi(float2 (&v)[NR], unsigned mask, const int (&cls)[RB], float u0,
+                                                float s0, float u1, float s1) {
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+        const float u = cls[k] ? u1 : u0;
+        const float s = cls[k] ? s1 : s0;
+        const float2 nu = make_float2(-u, -u), ps = make_float2(s, s), ns = make_float2(-s, -s);
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (!((r >> k) & 1)) rrot(v[r], v[r | (1 << k)], nu, ps, ns);
+    }
+}
+
+// v * i^k
+__device__ __forceinline__ float2 mul_ipow(float2 v, int k) {
+    float2 r = (k & 1) ? make_float2(-v.y, v.x) : v;
+    if (k & 2) { r.x = -r.x; r.y = -r.y; }
+    return r;
+}
 
 template <int NBUF>
 __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__restrict__ psi, const double *__restrict__ recs,
@@ -215,46 +261,38 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         // ---- stage A: registers = local 8..11 ----
 #pragma unroll
         for (int r = 0; r < NR; ++r) v[r] = tb[a_base + (r << TB)];
-        rotate_regs<float>(v, P.rot[0], cls0, u0, s0, u1, s1, had);
+        const int pc_tile = __popcll(tile & tmask);
+        if (P.frame & 2) {
+            const int k0 = __popc(t) + pc_tile;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) v[r] = mul_ipow(v[r], k0 + __popc(r));
+        }
+        if (P.frame & 1) rotate_regs_phi(v, P.rot[0], cls0, u0, s0, u1, s1);
+        else rotate_regs<float>(v, P.rot[0], cls0, u0, s0, u1, s1, had);
 #pragma unroll
         for (int r = 0; r < NR; ++r) tb[a_base + (r << TB)] = v[r];
         __syncthreads();
         // ---- stage B: registers = local 0..3 (16-byte accesses) ----
         if (P.stage_b) {
             float4 *tb4 = reinterpret_cast<float4 *>(tb);
-            if (!had) {
-                // A rotation butterfly is symmetric in its two amplitudes, so the
-                // thread may hold its eight float4 slots in physical order: slot j
-                // carries local bits 1..3 equal to j ^ (t & 7), and every pair of
-                // registers differing in one bit is still a pair of that qubit.
 #pragma unroll
-                for (int m = 0; m < NR / 2; ++m) {
-                    float4 q = tb4[b_base + m];
-                    v[2 * m] = make_float2(q.x, q.y);
-                    v[2 * m + 1] = make_float2(q.z, q.w);
-                }
-                rotate_regs<float>(v, P.rot[1], cls1, u0, s0, u1, s1, false);
-#pragma unroll
-                for (int m = 0; m < NR / 2; ++m)
-                    tb4[b_base + m] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
-            } else {
-#pragma unroll
-                for (int m = 0; m < NR / 2; ++m) {
-                    float4 q = tb4[b_base + (m ^ b_x)];
-                    v[2 * m] = make_float2(q.x, q.y);
-                    v[2 * m + 1] = make_float2(q.z, q.w);
-                }
-                rotate_regs<float>(v, P.rot[1], cls1, u0, s0, u1, s1, true);
-#pragma unroll
-                for (int m = 0; m < NR / 2; ++m)
-                    tb4[b_base + (m ^ b_x)] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
+            for (int m = 0; m < NR / 2; ++m) {
+                float4 q = tb4[b_base + (m ^ b_x)];
+                v[2 * m] = make_float2(q.x, q.y);
+                v[2 * m + 1] = make_float2(q.z, q.w);
             }
+            if (P.frame & 1) rotate_regs_phi(v, P.rot[1], cls1, u0, s0, u1, s1);
+            else rotate_regs<float>(v, P.rot[1], cls1, u0, s0, u1, s1, had);
+#pragma unroll
+            for (int m = 0; m < NR / 2; ++m)
+                tb4[b_base + (m ^ b_x)] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
             __syncthreads();
         }
         // ---- stage C: registers = local 4..7; diagonal phase; store ----
 #pragma unroll
         for (int r = 0; r < NR; ++r) v[r] = tb[c_base[r & 7] + (r << 4)];
-        rotate_regs<float>(v, P.rot[2], cls2, u0, s0, u1, s1, had);
+        if (P.frame & 1) rotate_regs_phi(v, P.rot[2], cls2, u0, s0, u1, s1);
+        else rotate_regs<float>(v, P.rot[2], cls2, u0, s0, u1, s1, had);
         // global base of the tile: mid bits -> global c.., upper bits (and batch) -> next+k..
         const long long mid = tile & ((1ll << P.mid_bits) - 1);
         const long long up = tile >> P.mid_bits;
@@ -271,6 +309,11 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
 #pragma unroll
                 for (int r = 0; r < NR; ++r) { v[r].x *= P.scale; v[r].y *= P.scale; }
             }
+        }
+        if (P.frame & 4) {
+            const int k0 = -(__popc(tlo) + __popc(thi) + pc_tile);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) v[r] = mul_ipow(v[r], (k0 - __popc(r)) & 3);
         }
         float2 *dst = psi + gbase + toff;
 #pragma unroll
