@@ -132,6 +132,23 @@ __device__ __forceinline__ void rotate_regs_phi(float2 (&v)[NR], unsigned mask, 
     }
 }
 
+// unnormalised Hadamard butterflies with packed FP32x2: (a, b) <- (a + b, a - b)
+__device__ __forceinline__ void hadamard_regs2(float2 (&v)[NR], unsigned mask) {
+    const float2 one = make_float2(1.f, 1.f), mone = make_float2(-1.f, -1.f);
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (!((r >> k) & 1)) {
+                const int q = r | (1 << k);
+                const float2 a = v[r], b = v[q];
+                v[r] = fma2(one, a, b);
+                v[q] = fma2(mone, b, a);
+            }
+    }
+}
+
 // v * i^k
 __device__ __forceinline__ float2 mul_ipow(float2 v, int k) {
     float2 r = (k & 1) ? make_float2(-v.y, v.x) : v;
@@ -268,7 +285,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             for (int r = 0; r < NR; ++r) v[r] = mul_ipow(v[r], k0 + __popc(r));
         }
         if (P.frame & 1) rotate_regs_phi(v, P.rot[0], cls0, u0, s0, u1, s1);
-        else rotate_regs<float>(v, P.rot[0], cls0, u0, s0, u1, s1, had);
+        else if (had) hadamard_regs2(v, P.rot[0]);
+        else rotate_regs<float>(v, P.rot[0], cls0, u0, s0, u1, s1, false);
 #pragma unroll
         for (int r = 0; r < NR; ++r) tb[a_base + (r << TB)] = v[r];
         __syncthreads();
@@ -282,7 +300,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                 v[2 * m + 1] = make_float2(q.z, q.w);
             }
             if (P.frame & 1) rotate_regs_phi(v, P.rot[1], cls1, u0, s0, u1, s1);
-            else rotate_regs<float>(v, P.rot[1], cls1, u0, s0, u1, s1, had);
+            else if (had) hadamard_regs2(v, P.rot[1]);
+            else rotate_regs<float>(v, P.rot[1], cls1, u0, s0, u1, s1, false);
 #pragma unroll
             for (int m = 0; m < NR / 2; ++m)
                 tb4[b_base + (m ^ b_x)] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
@@ -292,7 +311,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
 #pragma unroll
         for (int r = 0; r < NR; ++r) v[r] = tb[c_base[r & 7] + (r << 4)];
         if (P.frame & 1) rotate_regs_phi(v, P.rot[2], cls2, u0, s0, u1, s1);
-        else rotate_regs<float>(v, P.rot[2], cls2, u0, s0, u1, s1, had);
+        else if (had) hadamard_regs2(v, P.rot[2]);
+        else rotate_regs<float>(v, P.rot[2], cls2, u0, s0, u1, s1, false);
         // global base of the tile: mid bits -> global c.., upper bits (and batch) -> next+k..
         const long long mid = tile & ((1ll << P.mid_bits) - 1);
         const long long up = tile >> P.mid_bits;
