@@ -89,7 +89,7 @@ typedef enum {
     QS_OPT_XPASS = 4,         /* X-pass kernel for complex64: 0 auto (TMA), 1 the
                                  register-staged kernel, 2 the persistent TMA kernel */
     QS_OPT_TMA_BUFFERS = 5    /* shared-memory tile buffers per CTA of the TMA kernel:
-                                 2 (default) or 3                                    */
+                                 2 or 3 (default)                                    */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open

@@ -82,7 +82,7 @@ struct qs_sim {
     long long launches = 0;
     // persistent TMA X pass (complex64)
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
-    int nbuf = 2;                          // TMA shared-memory buffers per CTA (2 or 3)
+    int nbuf = 3;                          // TMA shared-memory buffers per CTA (2 or 3)
     int sm_count = 0;
     std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
     std::vector<CUtensorMap> tmaps;        // one per pass, encoded for the bound state

@@ -106,6 +106,30 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
     return d;
 }
 
+typedef unsigned long long u64;
+
+__device__ __forceinline__ u64 pk(float x, float y) {
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+    return r;
+}
+
+// packed FP32x2 FMA on register pairs
+__device__ __forceinline__ u64 fma2p(u64 a, u64 b, u64 c) {
+    u64 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ void rrotp(u64 &a, u64 &b, u64 nu, u64 ps, u64 ns) {
+    const u64 ta = fma2p(nu, a, a);
+    const u64 tb = fma2p(nu, b, b);
+    const u64 na = fma2p(ps, b, ta);
+    const u64 nb = fma2p(ns, a, tb);
+    a = na;
+    b = nb;
+}
+
 // In the frame phi_i = i^{popcount(i)} psi_i, exp(i theta X_q) becomes the real rotation
 // [[cos, sin], [-sin, cos]] (S X S^dagger = Y with S = diag(1, i)), which treats the real
 // and imaginary parts alike:  a' = a - u a + s b,  b' = b - u b - s a  (cos = 1 - u).
@@ -120,16 +144,22 @@ __device__ __forceinline__ void rrot(float2 &a, float2 &b, float2 nu, float2 ps,
 
 __device__ __forceinline__ void rotate_regs_phi(float2 (&v)[NR], unsigned mask, const int (&cls)[RB], float u0,
                                                 float s0, float u1, float s1) {
+    u64 w[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) w[r] = pk(v[r].x, v[r].y);
+    const u64 nu0 = pk(-u0, -u0), ps0 = pk(s0, s0), ns0 = pk(-s0, -s0);
+    const u64 nu1 = pk(-u1, -u1), ps1 = pk(s1, s1), ns1 = pk(-s1, -s1);
 #pragma unroll
     for (int k = 0; k < RB; ++k) {
         if (!((mask >> k) & 1u)) continue;
-        const float u = cls[k] ? u1 : u0;
-        const float s = cls[k] ? s1 : s0;
-        const float2 nu = make_float2(-u, -u), ps = make_float2(s, s), ns = make_float2(-s, -s);
+        const bool c = cls[k] != 0;
+        const u64 nu = c ? nu1 : nu0, ps = c ? ps1 : ps0, ns = c ? ns1 : ns0;
 #pragma unroll
         for (int r = 0; r < NR; ++r)
-            if (!((r >> k) & 1)) rrot(v[r], v[r | (1 << k)], nu, ps, ns);
+            if (!((r >> k) & 1)) rrotp(w[r], w[r | (1 << k)], nu, ps, ns);
     }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) asm("mov.b64 {%0, %1}, %2;" : "=f"(v[r].x), "=f"(v[r].y) : "l"(w[r]));
 }
 
 // unnormalised Hadamard butterflies with packed FP32x2: (a, b) <- (a + b, a - b)
