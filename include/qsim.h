@@ -89,7 +89,7 @@ typedef enum {
     QS_OPT_XPASS = 4,         /* X-pass kernel for complex64: 0 auto (TMA), 1 the
                                  register-staged kernel, 2 the persistent TMA kernel */
     QS_OPT_TMA_BUFFERS = 5    /* shared-memory tile buffers per CTA of the TMA kernel:
-                                 2 or 3 (default)                                    */
+                                 2 (default) or 3                                    */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open
@@ -177,6 +177,14 @@ qs_status qs_scan(qs_sim *sim, const qs_couplings *points, int n_points, const d
 /* Synchronise the bound stream and report device-side failures: QS_ERR_CUDA for
  * a failed launch, QS_ERR_TIMEOUT if a bounded wait inside a kernel gave up. */
 qs_status qs_sync(qs_sim *sim);
+
+/* Autotuner: times n_steps second-order steps of every X-pass configuration that
+ * applies (complex64: the persistent TMA kernel with 2 or 3 tile buffers, and the
+ * register-staged kernel; complex128: the register-staged kernel) on the bound
+ * state, which is overwritten, and keeps the fastest (QS_OPT_XPASS,
+ * QS_OPT_TMA_BUFFERS).  Outputs the choice and its ms per step (host). */
+qs_status qs_autotune(qs_sim *sim, int n_steps, int *best_xpass, int *best_buffers,
+                      double *best_ms_per_step);
 
 /* Failure-detection self-test: launches a kernel that waits on an mbarrier which
  * never completes, with the same bounded wait as the TMA X pass, limited to

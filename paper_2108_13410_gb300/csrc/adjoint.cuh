@@ -285,6 +285,78 @@ __global__ void __launch_bounds__(NT) k_apply_h_pass(const typename C2<R>::T *__
     }
 }
 
+// Read-only X measurement on the tiled passes: for every qubit of the pass, in the
+// stage where it is a register bit, sum Re(conj(a) b) over its amplitude pairs, i.e.
+// <X_q> / 2, accumulated per X class.  partials[(b * nblk + slot0 + blockIdx.x) * RED_NV + {0, 1}].
+template <typename R>
+__global__ void __launch_bounds__(NT) k_xmeasure(const typename C2<R>::T *__restrict__ psi, long long state_stride,
+                                                 long long ntiles, const PassDesc *__restrict__ d,
+                                                 double *__restrict__ partials, int nblk, int slot0) {
+    using V = typename C2<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V *tp = reinterpret_cast<V *>(smem_raw);
+    const int t = threadIdx.x;
+    psi += (long long)blockIdx.y * state_stride;
+    int lm[LT];
+#pragma unroll
+    for (int j = 0; j < LT; ++j) lm[j] = d->lmap[j];
+    const unsigned rm0 = d->rot_mask[0], rm1 = d->rot_mask[1], rm2 = d->rot_mask[2];
+    int cls[3][RB];
+#pragma unroll
+    for (int st = 0; st < 3; ++st)
+#pragma unroll
+        for (int k = 0; k < RB; ++k) cls[st][k] = d->reg_cls[st][k];
+    const int nfixed = d->nfixed;
+    double acc[2] = {0.0, 0.0};
+    auto pairs = [&](const V (&v)[NR], unsigned mask, const int (&c)[RB], R &g0, R &g1) {
+#pragma unroll
+        for (int k = 0; k < RB; ++k) {
+            if (!((mask >> k) & 1u)) continue;
+            R g = 0;
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                if (!((r >> k) & 1)) g += v[r].x * v[r | (1 << k)].x + v[r].y * v[r | (1 << k)].y;
+            if (c[k]) g1 += g; else g0 += g;
+        }
+    };
+    for (long long tau = blockIdx.x; tau < ntiles; tau += gridDim.x) {
+        long long base = 0;
+        for (int k = 0; k < nfixed; ++k)
+            if ((tau >> k) & 1) base |= 1ll << d->fixed_pos[k];
+        R g0 = 0, g1 = 0;
+        V v[NR];
+        long long toff = base;
+#pragma unroll
+        for (int j = 0; j < TB; ++j)
+            if ((t >> j) & 1) toff |= 1ll << lm[j];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            long long off = toff;
+#pragma unroll
+            for (int k = 0; k < RB; ++k)
+                if ((r >> k) & 1) off |= 1ll << lm[TB + k];
+            v[r] = psi[off];
+        }
+        pairs(v, rm0, cls[0], g0, g1);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) tp[swz(t | (r << TB))] = v[r];
+        __syncthreads();
+        if (rm1) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r) v[r] = tp[swz(r | (t << RB))];
+            pairs(v, rm1, cls[1], g0, g1);
+        }
+        const int tlo = t & 15, thi = t >> 4;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) v[r] = tp[swz(tlo | (r << 4) | (thi << 8))];
+        pairs(v, rm2, cls[2], g0, g1);
+        acc[0] += (double)g0;
+        acc[1] += (double)g1;
+        __syncthreads();
+    }
+    block_store<2>(acc, partials + ((long long)blockIdx.y * nblk + slot0 + blockIdx.x) * RED_NV);
+}
+
 // lambda_b <- w_b * phi_b with w_b = (res[b * RED_NV], res[b * RED_NV + 1]) = <phi_b|psi_b>
 template <typename R>
 __global__ void k_scaled_copy(typename C2<R>::T *__restrict__ lam, const typename C2<R>::T *__restrict__ phi,

@@ -82,7 +82,7 @@ struct qs_sim {
     long long launches = 0;
     // persistent TMA X pass (complex64)
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
-    int nbuf = 3;                          // TMA shared-memory buffers per CTA (2 or 3)
+    int nbuf = 2;                          // TMA shared-memory buffers per CTA (2 or 3)
     int sm_count = 0;
     std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
     std::vector<CUtensorMap> tmaps;        // one per pass, encoded for the bound state
@@ -936,6 +936,7 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
         cudaFuncSetAttribute(k_adj_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_apply_h_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_apply_h_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
+        cudaFuncSetAttribute(k_xmeasure<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1 << LT) * 16));
     }
     size_t smem64 = (size_t)(1 << LT) * 16 + (size_t)s->max_lut * 16;
     cudaFuncSetAttribute(k_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
@@ -1130,8 +1131,30 @@ static qs_status expect_impl(qs_sim *s, int kind, int index, const qs_couplings 
             double sv = (kind == QS_ENERGY) ? 1.0 : sval;
             int slot = 0;
             if ((st = reduce_diag<R>(s, s->state[0], 0, slot++)) != QS_OK) return st;
-            for (int q = 0; q < s->n; ++q)
-                if ((st = xm(1ull << q, slot++)) != QS_OK) return st;
+            const int np = (int)s->passes.size();
+            int xslot = -1;
+            if (np > 0) {
+                // single-qubit X terms: one read-only sweep per pass, sums per class
+                const long long ntiles = 1ll << (s->n - LT);
+                const unsigned G = (unsigned)std::min<long long>(ntiles, (long long)s->sm_count * 4);
+                const size_t nblk = (size_t)np * G;
+                if ((st = grow(s, &s->d_adj_part, &s->adj_part_cap, nblk * B * RED_NV, false)) != QS_OK) return st;
+                const size_t smem = (size_t)(1 << LT) * sizeof(V<R>);
+                for (int p = 0; p < np; ++p) {
+                    k_xmeasure<R><<<dim3(G, B), NT, smem, s->stream>>>((const V<R> *)s->state[0], s->dim, ntiles,
+                                                                      s->d_passes + NVAR * p, s->d_adj_part,
+                                                                      (int)nblk, p * (int)G);
+                    CKL(s); s->launches++;
+                }
+                xslot = slot++;
+                k_finish<<<B, RED_THREADS, 0, s->stream>>>(s->d_adj_part, (int)nblk, 2,
+                                                           s->d_res + (size_t)xslot * B * RED_NV);
+                CKL(s); s->launches++;
+            }
+            const int q0 = slot;
+            if (np == 0)
+                for (int q = 0; q < s->n; ++q)
+                    if ((st = xm(1ull << q, slot++)) != QS_OK) return st;
             int star0 = slot;
             if (!L.gauge_higgs)
                 for (uint64_t m : L.stars)
@@ -1140,8 +1163,13 @@ static qs_status expect_impl(qs_sim *s, int kind, int index, const qs_couplings 
             for (int b = 0; b < B; ++b) {
                 Coef q = coefficients(c[b], sv);
                 double e = -q.za * res(s, 0, b, 1) - q.zb * res(s, 0, b, 2);
-                for (int k = 0; k < s->n; ++k)
-                    e -= (L.x_class[k] ? q.xt : q.xs) * res(s, 1 + k, b, 0);
+                if (xslot >= 0) {
+                    // each pair counted once: <X_q> = 2 sum_pairs Re(conj(a) b)
+                    e -= q.xs * 2.0 * res(s, xslot, b, 0) + q.xt * 2.0 * res(s, xslot, b, 1);
+                } else {
+                    for (int k = 0; k < s->n; ++k)
+                        e -= (L.x_class[k] ? q.xt : q.xs) * res(s, q0 + k, b, 0);
+                }
                 for (int k = star0; k < slot; ++k) e -= q.xt * res(s, k, b, 0);
                 out[b] = e;
             }
@@ -1304,6 +1332,46 @@ qs_status qs_scan(qs_sim *s, const qs_couplings *points, int n_points, const dou
         std::fill(tmp.begin(), tmp.end(), 0.0);
         put(7, tmp.data());
     }
+    return QS_OK;
+}
+
+qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers, double *best_ms_per_step) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (n_steps < 1 || n_steps > 1000) FAIL(s, QS_ERR_ARG, "n_steps must be in [1, 1000]");
+    if (!best_xpass || !best_buffers || !best_ms_per_step) FAIL(s, QS_ERR_ARG, "null output");
+    struct Cand { int xpass, nbuf; };
+    std::vector<Cand> cands;
+    if (s->dtype == QS_C64 && s->tmaps_ok) { cands.push_back({2, 2}); cands.push_back({2, 3}); }
+    cands.push_back({1, 2});
+    const int saved_method = s->method, saved_profile = s->profile, saved_graph = s->use_graph;
+    s->method = 0; s->profile = 0; s->use_graph = 0;
+    std::vector<qs_couplings> c(s->batch, qs_couplings{1.0, 1.0, 0.6, 0.6});
+    std::vector<double> sv(n_steps + 2);
+    for (int k = 0; k < n_steps + 2; ++k) sv[k] = (k + 0.5) / (n_steps + 2);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(s, cudaEventCreate(&e0));
+    CK(s, cudaEventCreate(&e1));
+    double best = 1e300;
+    Cand pick = cands.back();
+    for (const Cand &cd : cands) {
+        s->xpass_impl = cd.xpass; s->nbuf = cd.nbuf;
+        if ((st = qs_init_plus(s)) != QS_OK) break;
+        if ((st = qs_evolve(s, c.data(), sv.data(), 0.02, 2, 2)) != QS_OK) break;   // warm-up
+        CK(s, cudaEventRecord(e0, s->stream));
+        if ((st = qs_evolve(s, c.data(), sv.data() + 2, 0.02, n_steps, 2)) != QS_OK) break;
+        CK(s, cudaEventRecord(e1, s->stream));
+        CK(s, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(s, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; pick = cd; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->method = saved_method; s->profile = saved_profile; s->use_graph = saved_graph;
+    if (st != QS_OK) return st;
+    s->xpass_impl = pick.xpass; s->nbuf = pick.nbuf;
+    *best_xpass = pick.xpass; *best_buffers = pick.nbuf; *best_ms_per_step = best / n_steps;
     return QS_OK;
 }
 

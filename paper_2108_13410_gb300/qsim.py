@@ -65,6 +65,7 @@ _SIGS = {
     "qs_fidelity": ([_P, _P, _DP], _I),
     "qs_sync": ([_P], _I),
     "qs_selftest_wait": ([_P, _D], _I),
+    "qs_autotune": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _DP], _I),
     "qs_save": ([_P, ctypes.c_char_p], _I),
     "qs_load": ([_P, ctypes.c_char_p], _I),
     "qs_scan": ([_P, _CP, _I, _DP, _D, _I, _I, _DP], _I),
@@ -227,6 +228,13 @@ def qs_scan(sim, points, s: Sequence[float], dt: float, order: int = 2):
     return out
 
 
+def qs_autotune(sim, n_steps: int = 20):
+    """Returns (xpass kernel, tile buffers, ms per step) of the fastest configuration."""
+    xp, nb, ms = _I(), _I(), ctypes.c_double()
+    _check(sim, library().qs_autotune(sim, n_steps, ctypes.byref(xp), ctypes.byref(nb), ctypes.byref(ms)))
+    return xp.value, nb.value, ms.value
+
+
 def qs_selftest_wait(sim, limit_ms: float):
     _check(sim, library().qs_selftest_wait(sim, float(limit_ms)))
 
@@ -355,6 +363,37 @@ class Simulator:
 
     def sync(self):
         qs_sync(self.h)
+
+    def autotune(self, n_steps: int = 20, cache: bool = True):
+        """Pick the fastest X-pass configuration for this lattice, dtype and batch on
+        this GPU, remembering it in a JSON cache (QSIM_CACHE, default
+        ~/.cache/qsim_gb300/autotune.json).  Overwrites the state."""
+        import json
+        key = "|".join(str(x) for x in (self.torch.cuda.get_device_name(self.device), self.n, self.dtype_name,
+                                        self.form, self.batch))
+        path = os.environ.get("QSIM_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "qsim_gb300",
+                                                         "autotune.json"))
+        table = {}
+        if cache and os.path.exists(path):
+            try:
+                table = json.load(open(path))
+            except (OSError, ValueError):
+                table = {}
+        if cache and key in table:
+            xp, nb = table[key]["xpass"], table[key]["buffers"]
+            self.set_option(QS_OPT_XPASS, xp)
+            self.set_option(QS_OPT_TMA_BUFFERS, nb)
+            return table[key]
+        xp, nb, ms = qs_autotune(self.h, n_steps)
+        entry = {"xpass": xp, "buffers": nb, "ms_per_step": ms}
+        if cache:
+            table[key] = entry
+            try:
+                os.makedirs(os.path.dirname(path), exist_ok=True)
+                json.dump(table, open(path, "w"), indent=1)
+            except OSError:
+                pass
+        return entry
 
     def save(self, path):
         qs_save(self.h, path)

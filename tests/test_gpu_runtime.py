@@ -102,3 +102,36 @@ def test_launch_count_is_reported():
     sim.sync()
     # device-built records (1) + 3 passes x 10 steps + 3 trailing passes
     assert sim.launch_count() == 1 + 3 * 11
+
+
+@gpu
+def test_autotune_picks_a_valid_configuration(tmp_path, monkeypatch):
+    monkeypatch.setenv("QSIM_CACHE", str(tmp_path / "tune.json"))
+    sim = _sim(3, 3, form="gh", dtype="c64")
+    e = sim.autotune(n_steps=4)
+    assert e["xpass"] in (1, 2) and e["buffers"] in (2, 3) and e["ms_per_step"] > 0
+    again = sim.autotune(n_steps=4)           # from the cache
+    assert again["xpass"] == e["xpass"] and again["buffers"] == e["buffers"]
+    # the chosen configuration still evolves correctly
+    lat = OracleLattice(3, 3, True, "ug")
+    s = O.schedule_linear(20.0, 1000)[:10]
+    ref = O.evolve(lat, Couplings(0.6, 0.6), s, 0.02, 2)
+    sim.init_plus()
+    sim.evolve([(0.6, 0.6)], s, 0.02, 2)
+    sl = sim.state[0, : 1 << 18].cpu().numpy().astype(np.complex128) * 2 ** 4.5
+    assert np.linalg.norm(sl - ref) <= 1e-5
+
+
+@gpu
+def test_energy_from_tiled_x_measurement_matches_oracle():
+    """QS_ENERGY uses the read-only tiled X sweep for n >= 12; check it on 18 and 27 qubits
+    against the oracle's term-by-term energy (27 qubits through the unitary-gauge slice)."""
+    lat = OracleLattice(3, 2, True, "gh")
+    s = O.schedule_linear(2.0, 20)
+    ref = O.evolve(lat, Couplings(0.9, 0.4), s, 0.1, 2)
+    for dtype, tol in (("c128", 1e-9), ("c64", 1e-4)):
+        sim = _sim(3, 2, form="gh", dtype=dtype)
+        sim.init_plus()
+        sim.evolve([(0.9, 0.4)], s, 0.1, 2)
+        assert abs(sim.energy([(0.9, 0.4)])[0] - O.energy(ref, lat, Couplings(0.9, 0.4))) <= tol
+        assert abs(sim.energy([(0.9, 0.4)], s=0.3)[0] - O.energy(ref, lat, Couplings(0.9, 0.4), 0.3)) <= tol
