@@ -124,8 +124,9 @@ def test_autotune_picks_a_valid_configuration(tmp_path, monkeypatch):
 
 @gpu
 def test_energy_from_tiled_x_measurement_matches_oracle():
-    """QS_ENERGY uses the read-only tiled X sweep for n >= 12; check it on 18 and 27 qubits
-    against the oracle's term-by-term energy (27 qubits through the unitary-gauge slice)."""
+    """QS_ENERGY uses the read-only tiled X sweep for n >= 12; check it on 18 qubits against
+    the oracle's term-by-term energy, and on 27 qubits against the 18-qubit unitary-gauge
+    oracle (a gauge-invariant gauge-Higgs state has the energy of its unitary-gauge image)."""
     lat = OracleLattice(3, 2, True, "gh")
     s = O.schedule_linear(2.0, 20)
     ref = O.evolve(lat, Couplings(0.9, 0.4), s, 0.1, 2)
@@ -135,3 +136,11 @@ def test_energy_from_tiled_x_measurement_matches_oracle():
         sim.evolve([(0.9, 0.4)], s, 0.1, 2)
         assert abs(sim.energy([(0.9, 0.4)])[0] - O.energy(ref, lat, Couplings(0.9, 0.4))) <= tol
         assert abs(sim.energy([(0.9, 0.4)], s=0.3)[0] - O.energy(ref, lat, Couplings(0.9, 0.4), 0.3)) <= tol
+
+    ug = OracleLattice(3, 3, True, "ug")
+    s27 = O.schedule_linear(20.0, 1000)[:10]
+    ref27 = O.evolve(ug, Couplings(0.6, 0.6), s27, 0.02, 2)
+    sim = _sim(3, 3, form="gh", dtype="c64")
+    sim.init_plus()
+    sim.evolve([(0.6, 0.6)], s27, 0.02, 2)
+    assert abs(sim.energy([(0.6, 0.6)])[0] - O.energy(ref27, ug, Couplings(0.6, 0.6))) <= 2 * 50 * 1e-5
