@@ -322,6 +322,9 @@ def run_ours(args):
         del sp
         torch.cuda.empty_cache()
 
+    if rank == 0 and not args.no_accuracy:
+        extra["accuracy"] = accuracy_leg(local, dev)
+
     if rank == 0 and not args.no_scan:
         extra["scan"] = scan_leg(local, dev)
 
@@ -350,6 +353,43 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def accuracy_leg(local, dev, n_steps=1000):
+    """Error of the complex64 27-qubit evolution against the FP64 oracle over the full
+    1000-step schedule.  The oracle runs the 18-qubit unitary-gauge image: a
+    gauge-invariant gauge-Higgs state restricted to tau = 0 and scaled by 2^{9/2} is
+    the unitary-gauge state, and both have the same energy."""
+    import torch
+    from oracle import OracleLattice, Couplings
+    from oracle import core as O
+    from paper_2108_13410_gb300 import Simulator
+    W = WORKLOAD
+    dt = W["T"] / W["total_steps"]
+    s = linear_midpoints(W["T"], W["total_steps"])[:n_steps]
+    cpl = [(W["g"], W["lam"])]
+    ug = OracleLattice(W["Lx"], W["Ly"], True, "ug")
+    c = Couplings(W["g"], W["lam"])
+    t0 = time.perf_counter()
+    ref = O.evolve(ug, c, s, dt, W["order"])
+    e_ref = O.energy(ref, ug, c)
+    oracle_s = time.perf_counter() - t0
+    out = {"steps": n_steps, "oracle": "18-qubit unitary-gauge FP64 oracle", "oracle_seconds": oracle_s,
+           "oracle_energy": e_ref}
+    for renorm in (0, 50):
+        sim = Simulator(W["Lx"], W["Ly"], form=W["form"], dtype="c64", device=f"cuda:{local}",
+                        renorm_every=renorm)
+        sim.init_plus()
+        sim.evolve(cpl, s, dt, W["order"])
+        e = float(sim.energy(cpl)[0])
+        sl = sim.state[0, : 1 << 18].to(torch.complex128).cpu().numpy() * 2 ** 4.5
+        rel = float(np.linalg.norm(sl - ref) / np.linalg.norm(ref))
+        mx = float(np.max(np.abs(sl - ref)) / np.max(np.abs(ref)))
+        out[f"c64_renorm{renorm}"] = {"amp_rel_l2": rel, "amp_rel_max": mx, "energy": e,
+                                     "energy_abs_err": abs(e - e_ref)}
+        del sim
+        torch.cuda.empty_cache()
+    return out
 
 
 def scan_leg(local, dev, chunk=64):
@@ -445,6 +485,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--adjoint-steps", type=int, default=500)
     ap.add_argument("--no-scan", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pergate", action="store_true")
     ap.add_argument("--source-hash", action="store_true", help="print the X-pass kernel source hash")
