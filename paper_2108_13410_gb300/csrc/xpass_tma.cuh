@@ -179,6 +179,44 @@ __device__ __forceinline__ void hadamard_regs2(float2 (&v)[NR], unsigned mask) {
     }
 }
 
+__device__ __forceinline__ float2 unpk(u64 w) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(w));
+    return v;
+}
+
+// Real-frame rotations on packed register pairs; per class the constants
+// (-u, -u), (s, s), (-s, -s) are prepared once per operator record.
+struct RotConst { u64 nu[2], ps[2], ns[2]; };
+
+__device__ __forceinline__ void rotate_w(u64 (&w)[NR], unsigned mask, const int (&cls)[RB], const RotConst &C) {
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+        const bool c = cls[k] != 0;
+        const u64 nu = c ? C.nu[1] : C.nu[0], ps = c ? C.ps[1] : C.ps[0], ns = c ? C.ns[1] : C.ns[0];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (!((r >> k) & 1)) rrotp(w[r], w[r | (1 << k)], nu, ps, ns);
+    }
+}
+
+__device__ __forceinline__ void hadamard_w(u64 (&w)[NR], unsigned mask) {
+    const u64 one = pk(1.f, 1.f), mone = pk(-1.f, -1.f);
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (!((r >> k) & 1)) {
+                const int q = r | (1 << k);
+                const u64 a = w[r], b = w[q];
+                w[r] = fma2p(one, a, b);
+                w[q] = fma2p(mone, b, a);
+            }
+    }
+}
+
 // v * i^k
 __device__ __forceinline__ float2 mul_ipow(float2 v, int k) {
     float2 r = (k & 1) ? make_float2(-v.y, v.x) : v;
@@ -268,6 +306,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
     const bool had = P.hadamard != 0;
     long long cur_batch = -1;
     float u0 = 0.f, s0 = 0.f, u1 = 0.f, s1 = 0.f;
+    RotConst RC;
     int cls0[RB], cls1[RB], cls2[RB];
 #pragma unroll
     for (int kk = 0; kk < RB; ++kk) {
@@ -285,6 +324,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             __syncthreads();
             const double *rec = recs + batch * rec_stride;
             u0 = (float)rec[0]; s0 = (float)rec[1]; u1 = (float)rec[2]; s1 = (float)rec[3];
+            RC.nu[0] = pk(-u0, -u0); RC.ps[0] = pk(s0, s0); RC.ns[0] = pk(-s0, -s0);
+            RC.nu[1] = pk(-u1, -u1); RC.ps[1] = pk(s1, s1); RC.ns[1] = pk(-s1, -s1);
             if (P.apply_z)
                 for (int i = t; i < nlut; i += NT)
                     lut[i] = make_float2((float)rec[P.lut_off + 2 * i], (float)rec[P.lut_off + 2 * i + 1]);
@@ -303,71 +344,77 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         if (!s_ok) return;
         if (t == 0 && it + NBUF - 1 < n_my) issue(it + NBUF - 1);
 
-        float2 *tb = buf + (size_t)b * (1 << LT);
-        float2 v[NR];
+        u64 *tb = reinterpret_cast<u64 *>(buf + (size_t)b * (1 << LT));
+        u64 w[NR];
         // ---- stage A: registers = local 8..11 ----
 #pragma unroll
-        for (int r = 0; r < NR; ++r) v[r] = tb[a_base + (r << TB)];
+        for (int r = 0; r < NR; ++r) w[r] = tb[a_base + (r << TB)];
         const int pc_tile = __popcll(tile & tmask);
         if (P.frame & 2) {
             const int k0 = __popc(t) + pc_tile;
 #pragma unroll
-            for (int r = 0; r < NR; ++r) v[r] = mul_ipow(v[r], k0 + __popc(r));
+            for (int r = 0; r < NR; ++r) {
+                const float2 v = mul_ipow(unpk(w[r]), k0 + __popc(r));
+                w[r] = pk(v.x, v.y);
+            }
         }
-        if (P.frame & 1) rotate_regs_phi(v, P.rot[0], cls0, u0, s0, u1, s1);
-        else if (had) hadamard_regs2(v, P.rot[0]);
-        else rotate_regs<float>(v, P.rot[0], cls0, u0, s0, u1, s1, false);
+        if (P.frame & 1) rotate_w(w, P.rot[0], cls0, RC);
+        else hadamard_w(w, P.rot[0]);
 #pragma unroll
-        for (int r = 0; r < NR; ++r) tb[a_base + (r << TB)] = v[r];
+        for (int r = 0; r < NR; ++r) tb[a_base + (r << TB)] = w[r];
         __syncthreads();
         // ---- stage B: registers = local 0..3 (16-byte accesses) ----
         if (P.stage_b) {
-            float4 *tb4 = reinterpret_cast<float4 *>(tb);
+            ulonglong2 *tb2 = reinterpret_cast<ulonglong2 *>(tb);
 #pragma unroll
             for (int m = 0; m < NR / 2; ++m) {
-                float4 q = tb4[b_base + (m ^ b_x)];
-                v[2 * m] = make_float2(q.x, q.y);
-                v[2 * m + 1] = make_float2(q.z, q.w);
+                const ulonglong2 q = tb2[b_base + (m ^ b_x)];
+                w[2 * m] = q.x;
+                w[2 * m + 1] = q.y;
             }
-            if (P.frame & 1) rotate_regs_phi(v, P.rot[1], cls1, u0, s0, u1, s1);
-            else if (had) hadamard_regs2(v, P.rot[1]);
-            else rotate_regs<float>(v, P.rot[1], cls1, u0, s0, u1, s1, false);
+            if (P.frame & 1) rotate_w(w, P.rot[1], cls1, RC);
+            else hadamard_w(w, P.rot[1]);
 #pragma unroll
-            for (int m = 0; m < NR / 2; ++m)
-                tb4[b_base + (m ^ b_x)] = make_float4(v[2 * m].x, v[2 * m].y, v[2 * m + 1].x, v[2 * m + 1].y);
+            for (int m = 0; m < NR / 2; ++m) tb2[b_base + (m ^ b_x)] = make_ulonglong2(w[2 * m], w[2 * m + 1]);
             __syncthreads();
         }
         // ---- stage C: registers = local 4..7; diagonal phase; store ----
 #pragma unroll
-        for (int r = 0; r < NR; ++r) v[r] = tb[c_base[r & 7] + (r << 4)];
-        if (P.frame & 1) rotate_regs_phi(v, P.rot[2], cls2, u0, s0, u1, s1);
-        else if (had) hadamard_regs2(v, P.rot[2]);
-        else rotate_regs<float>(v, P.rot[2], cls2, u0, s0, u1, s1, false);
+        for (int r = 0; r < NR; ++r) w[r] = tb[c_base[r & 7] + (r << 4)];
+        if (P.frame & 1) rotate_w(w, P.rot[2], cls2, RC);
+        else hadamard_w(w, P.rot[2]);
         // global base of the tile: mid bits -> global c.., upper bits (and batch) -> next+k..
         const long long mid = tile & ((1ll << P.mid_bits) - 1);
         const long long up = tile >> P.mid_bits;
         const long long gbase = (mid << P.c) + (up << (P.next + P.k));
-        if (P.apply_z) {
-            const long long tin = tile & tmask;                       // parity ignores batch
-            uint2 e0 = ptab[tin & 255], e1 = ptab[256 + ((tin >> 8) & 255)], e2 = ptab[512 + ((tin >> 16) & 255)];
-            const uint32_t pa = pa_t ^ e0.x ^ e1.x ^ e2.x;
-            const uint32_t pb = pb_t ^ e0.y ^ e1.y ^ e2.y;
+        if (P.apply_z || (P.frame & 4)) {
+            float2 v[NR];
 #pragma unroll
-            for (int r = 0; r < NR; ++r)
-                v[r] = cphase(v[r], lut[__popc(pa ^ P.pa_reg[r]) * nB1 + __popc(pb ^ P.pb_reg[r])]);
-            if (P.scale != 1.0f) {
+            for (int r = 0; r < NR; ++r) v[r] = unpk(w[r]);
+            if (P.apply_z) {
+                const long long tin = tile & tmask;                       // parity ignores batch
+                uint2 e0 = ptab[tin & 255], e1 = ptab[256 + ((tin >> 8) & 255)], e2 = ptab[512 + ((tin >> 16) & 255)];
+                const uint32_t pa = pa_t ^ e0.x ^ e1.x ^ e2.x;
+                const uint32_t pb = pb_t ^ e0.y ^ e1.y ^ e2.y;
 #pragma unroll
-                for (int r = 0; r < NR; ++r) { v[r].x *= P.scale; v[r].y *= P.scale; }
+                for (int r = 0; r < NR; ++r)
+                    v[r] = cphase(v[r], lut[__popc(pa ^ P.pa_reg[r]) * nB1 + __popc(pb ^ P.pb_reg[r])]);
+                if (P.scale != 1.0f) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) { v[r].x *= P.scale; v[r].y *= P.scale; }
+                }
             }
-        }
-        if (P.frame & 4) {
-            const int k0 = -(__popc(tlo) + __popc(thi) + pc_tile);
+            if (P.frame & 4) {
+                const int k0 = -(__popc(tlo) + __popc(thi) + pc_tile);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) v[r] = mul_ipow(v[r], (k0 - __popc(r)) & 3);
-        }
-        float2 *dst = psi + gbase + toff;
+                for (int r = 0; r < NR; ++r) v[r] = mul_ipow(v[r], (k0 - __popc(r)) & 3);
+            }
 #pragma unroll
-        for (int r = 0; r < NR; ++r) dst[P.roff_c[r]] = v[r];
+            for (int r = 0; r < NR; ++r) w[r] = pk(v[r].x, v[r].y);
+        }
+        u64 *dst = reinterpret_cast<u64 *>(psi + gbase + toff);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) dst[P.roff_c[r]] = w[r];
     }
 }
 
