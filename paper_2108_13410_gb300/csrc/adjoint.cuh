@@ -50,7 +50,7 @@ __device__ __forceinline__ void adj_stage(V (&p)[NR], V (&l)[NR], unsigned mask,
 // tiles).  zinv: first undo the Z layer (phase table conjugated) and accumulate the
 // Z-group values.  partials[(b * nblk + slot0 + blockIdx.x) * RED_NV + v].
 template <typename R>
-__global__ void __launch_bounds__(NT) k_adj_xpass(typename C2<R>::T *__restrict__ psi,
+__global__ void __launch_bounds__(NT, sizeof(R) == 4 ? 2 : 1) k_adj_xpass(typename C2<R>::T *__restrict__ psi,
                                                   typename C2<R>::T *__restrict__ lam, long long state_stride,
                                                   long long ntiles, const double *__restrict__ recs,
                                                   int rec_stride, const PassDesc *__restrict__ d, int zinv,
