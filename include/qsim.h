@@ -178,6 +178,15 @@ qs_status qs_scan(qs_sim *sim, const qs_couplings *points, int n_points, const d
  * a failed launch, QS_ERR_TIMEOUT if a bounded wait inside a kernel gave up. */
 qs_status qs_sync(qs_sim *sim);
 
+/* Number of link (sigma) qubits of the lattice. */
+int qs_num_links(const qs_sim *sim);
+
+/* Density of states of Z~ = -sum_l sigma^z_l (Sec. V, the DOS analysis): for each
+ * batch element, out[b * (n_links + 1) + k] = sum of |psi_i|^2 over the amplitudes
+ * with exactly k links in sigma^z = -1, i.e. the weight of the Z~ eigenvalue
+ * 2k - n_links.  FP64, host output; synchronises the stream. */
+qs_status qs_dos(qs_sim *sim, double *out);
+
 /* Autotuner: times n_steps second-order steps of every X-pass configuration that
  * applies (complex64: the persistent TMA kernel with 2 or 3 tile buffers, and the
  * register-staged kernel; complex128: the register-staged kernel) on the bound

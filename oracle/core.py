@@ -331,3 +331,15 @@ def fidelity_gradient(lat, c, s_list, dt, order, ds_dp, phi, psi0=None):
     g = np.array([2.0 * (ov.conjugate() * inner(phi, np.ascontiguousarray(d))).real
                   for d in dpsi])
     return abs(ov) ** 2, g
+
+
+def dos(psi, lat: OracleLattice) -> np.ndarray:
+    """Density of states of Z~ = -sum_l sigma^z_l (Sec. V): weight of the eigenvalue
+    Z~ = 2k - n_links, i.e. the sum of |psi_i|^2 over indices i with k link bits set."""
+    links = lat.link_qubits
+    out = np.zeros(len(links) + 1)
+    p = np.abs(np.asarray(psi)) ** 2
+    for i in range(p.size):
+        k = sum((i >> q) & 1 for q in links)
+        out[k] += p[i]
+    return out

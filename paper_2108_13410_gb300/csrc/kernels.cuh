@@ -582,3 +582,40 @@ __global__ void k_build_records(RecGeom G, const DevCouplings *__restrict__ cpl,
 }
 
 }  // namespace qsim
+
+namespace qsim {
+
+// Density of states of Z~ = -sum_l sigma^z_l (Sec. V): P(k) = sum over amplitudes with k
+// links in sigma^z = -1 of |psi_i|^2 (Z~ = 2k - n_links).  Per-block bins in shared
+// memory (FP64 atomics), then per-block partials; partials[(b * gridDim.x + blk) * nbins + k].
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_dos(const typename C2<R>::T *__restrict__ psi, int n,
+                                                     long long state_stride, unsigned long long linkmask, int nbins,
+                                                     double *__restrict__ partials) {
+    __shared__ double bins[64];
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x) bins[k] = 0.0;
+    __syncthreads();
+    psi += (long long)blockIdx.y * state_stride;
+    const long long dim = 1ll << n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dim;
+         i += (long long)gridDim.x * blockDim.x) {
+        auto a = psi[i];
+        double p = (double)a.x * (double)a.x + (double)a.y * (double)a.y;
+        atomicAdd(&bins[__popcll((unsigned long long)i & linkmask)], p);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nbins; k += blockDim.x)
+        partials[((long long)blockIdx.y * gridDim.x + blockIdx.x) * nbins + k] = bins[k];
+}
+
+// out[b * nval + v] = sum over nblk partials (layout [b][blk][v]), fixed order
+__global__ void k_finish_wide(const double *__restrict__ partials, int nblk, int nval, double *__restrict__ out) {
+    const int b = blockIdx.x;
+    for (int v = threadIdx.x; v < nval; v += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < nblk; ++k) s += partials[((long long)b * nblk + k) * nval + v];
+        out[(long long)b * nval + v] = s;
+    }
+}
+
+}  // namespace qsim

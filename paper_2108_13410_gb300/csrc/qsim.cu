@@ -1335,6 +1335,36 @@ qs_status qs_scan(qs_sim *s, const qs_couplings *points, int n_points, const dou
     return QS_OK;
 }
 
+int qs_num_links(const qs_sim *s) { return s ? s->lat.n_links : -1; }
+
+qs_status qs_dos(qs_sim *s, double *out) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (!out) FAIL(s, QS_ERR_ARG, "null output");
+    const int nbins = s->lat.n_links + 1, B = s->batch;
+    if (nbins > 64) FAIL(s, QS_ERR_ARG, "too many links");
+    uint64_t linkmask = 0;
+    for (int q = 0; q < s->n; ++q) if (!s->lat.x_class[q]) linkmask |= 1ull << q;
+    const int G = 152 * 4;
+    if ((st = grow(s, &s->d_adj_part, &s->adj_part_cap, (size_t)G * B * nbins + (size_t)B * nbins, false)) != QS_OK)
+        return st;
+    double *dout = s->d_adj_part + (size_t)G * B * nbins;
+    if (s->dtype == QS_C64)
+        k_dos<float><<<dim3(G, B), RED_THREADS, 0, s->stream>>>((const float2 *)s->state[0], s->n, s->dim, linkmask,
+                                                                nbins, s->d_adj_part);
+    else
+        k_dos<double><<<dim3(G, B), RED_THREADS, 0, s->stream>>>((const double2 *)s->state[0], s->n, s->dim,
+                                                                 linkmask, nbins, s->d_adj_part);
+    CKL(s); s->launches++;
+    k_finish_wide<<<B, 64, 0, s->stream>>>(s->d_adj_part, G, nbins, dout);
+    CKL(s); s->launches++;
+    CK(s, cudaMemcpyAsync(out, dout, (size_t)B * nbins * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(s, cudaStreamSynchronize(s->stream));
+    for (int i = 0; i < B * nbins; ++i)
+        if (!std::isfinite(out[i])) FAIL(s, QS_ERR_NONFINITE, "non-finite density of states");
+    return check_device_flag(s);
+}
+
 qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers, double *best_ms_per_step) {
     qs_status st;
     if ((st = check_ready(s)) != QS_OK) return st;

@@ -65,6 +65,8 @@ _SIGS = {
     "qs_fidelity": ([_P, _P, _DP], _I),
     "qs_sync": ([_P], _I),
     "qs_selftest_wait": ([_P, _D], _I),
+    "qs_num_links": ([_P], _I),
+    "qs_dos": ([_P, _DP], _I),
     "qs_autotune": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _DP], _I),
     "qs_save": ([_P, ctypes.c_char_p], _I),
     "qs_load": ([_P, ctypes.c_char_p], _I),
@@ -225,6 +227,18 @@ def qs_scan(sim, points, s: Sequence[float], dt: float, order: int = 2):
     out = np.zeros((len(points), QS_SCAN_NOBS), dtype=np.float64)
     _check(sim, library().qs_scan(sim, pts, len(points), sv.ctypes.data_as(_DP), dt, int(sv.size), order,
                                   out.ctypes.data_as(_DP)))
+    return out
+
+
+def qs_num_links(sim) -> int:
+    return library().qs_num_links(sim)
+
+
+def qs_dos(sim, batch: int = 1):
+    """Density of states of Z~ = -sum_l sigma^z_l: out[b, k] = weight of Z~ = 2k - n_links."""
+    nl = qs_num_links(sim)
+    out = np.zeros((batch, nl + 1), dtype=np.float64)
+    _check(sim, library().qs_dos(sim, out.ctypes.data_as(_DP)))
     return out
 
 
@@ -394,6 +408,9 @@ class Simulator:
             except OSError:
                 pass
         return entry
+
+    def dos(self):
+        return qs_dos(self.h, self.batch)
 
     def save(self, path):
         qs_save(self.h, path)
