@@ -116,6 +116,12 @@ qs_status qs_set_option(qs_sim *sim, int key, long long value);
 
 /* psi <- |+>^n for every batch element (ground state of H0). */
 qs_status qs_init_plus(qs_sim *sim);
+/* Toric-code ground states of Sec. IV (unitary-gauge form only), normalised in FP64:
+ * which = 0: psi_1, the projection of |+>^n onto B_p = +1 for every plaquette (Eq. (14));
+ * which = 1: psi_1', the projection of |0...0> onto A_v = +1 for every vertex (Eq. (15)),
+ * i.e. the uniform superposition over the star-flip orbit of |0...0> (on a torus: B_p = +1
+ * and both non-contractible Wilson loops +1). */
+qs_status qs_init_toric(qs_sim *sim, int which);
 /* Copy batch states between host memory (pinned for asynchronous transfer) and
  * the bound state; bytes must equal qs_state_bytes.  Synchronises the stream. */
 qs_status qs_upload_state(qs_sim *sim, const void *host, size_t bytes);
@@ -130,6 +136,12 @@ qs_status qs_trotter_step(qs_sim *sim, const qs_couplings *couplings, double s,
  * (the X-type terms commute), which leaves the product unchanged. */
 qs_status qs_evolve(qs_sim *sim, const qs_couplings *couplings, const double *s,
                     double dt, int n_steps, int order);
+
+/* Parameter path (Sec. III): n_steps Trotter steps of H1 with couplings that change
+ * from step to step, per_step[k * batch + b] for step k (no interpolation with H0,
+ * i.e. s = 1).  Otherwise as qs_evolve. */
+qs_status qs_evolve_path(qs_sim *sim, const qs_couplings *per_step, double dt, int n_steps,
+                         int order);
 
 /* Expectation value per batch element, accumulated in FP64 (out: host [batch]).
  * couplings and s are used by QS_ENERGY / QS_ENERGY_S only (may be NULL else). */

@@ -21,4 +21,5 @@ from .core import (Couplings, coefficients, plus_state, trotter_step, evolve,  #
                    schedule_linear, schedule_fourier, schedule_fourier_jacobian,
                    energy, observables, expect_x, expect_z, norm2, inner, fidelity,
                    apply_hamiltonian, energy_gradient, fidelity_gradient,
-                   evolve_with_tangents, set_threads, max_threads, dos)
+                   evolve_with_tangents, set_threads, max_threads, dos,
+                   evolve_path, toric_state)

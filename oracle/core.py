@@ -33,7 +33,7 @@ import os
 import numpy as np
 
 from . import build as _build
-from .lattice import OracleLattice
+from .lattice import OracleLattice, mask_of
 
 _LIB = None
 
@@ -343,3 +343,37 @@ def dos(psi, lat: OracleLattice) -> np.ndarray:
         k = sum((i >> q) & 1 for q in links)
         out[k] += p[i]
     return out
+
+
+def evolve_path(lat: OracleLattice, path, dt: float, order: int, psi0: np.ndarray | None = None,
+                callback=None) -> np.ndarray:
+    """Parameter path (Sec. III): step k is a Trotter step of H1 with couplings path[k]
+    (the Hamiltonian itself, s = 1)."""
+    psi = plus_state(lat.n_qubits) if psi0 is None else np.array(psi0, dtype=np.complex128)
+    for k, c in enumerate(path):
+        trotter_step(psi, lat, c, 1.0, dt, order)
+        if callback is not None:
+            callback(k, psi)
+    return psi
+
+
+def toric_state(lat: OracleLattice, which: int) -> np.ndarray:
+    """Toric-code ground states of Sec. IV, normalised.
+
+    which = 0: psi_1 = prod_p (1 + B_p)/2 |+...+>   (Eq. (14): the plaquette projections)
+    which = 1: psi_1' = prod_v (1 + A_v)/2 |0...0>  (Eq. (15): the star projections)
+    Each projector (1 + P)/2 is applied term by term with the Pauli-string primitives."""
+    n = lat.n_qubits
+    L = lib()
+    if which == 0:
+        psi = plus_state(n)
+        masks, axpy = lat.z_plaquettes(), L.or_axpy_zstring
+    else:
+        psi = np.zeros(1 << n, dtype=np.complex128)
+        psi[0] = 1.0
+        masks, axpy = [mask_of(s) for s in lat.stars], L.or_axpy_xstring
+    for m in masks:
+        out = 0.5 * psi
+        axpy(_p(out), _p(psi), n, int(m), 0.5)
+        psi = out
+    return psi / math.sqrt(norm2(psi))

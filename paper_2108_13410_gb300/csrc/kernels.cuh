@@ -495,6 +495,7 @@ namespace qsim {
 // ---------------------------------------------------------------------------
 struct RecGeom {
     int n_steps, order, fsal;    // fsal: second order with merged X half-steps
+    int path;                    // 1: couplings per step (cpl[k * batch + b]) with s = 1
     int batch, rec_stride;
     int nA, nB, nXA, nXB, xlut_off;
     int f32;
@@ -529,30 +530,41 @@ __device__ inline void dev_unit_pair(bool f32, double t, double *ou, double *os)
 //   order 1:      op k (< N): X theta(s_k) dt, Z at s_k
 //   second order: op k (<= N): X theta(s_k) dt/2 [k < N] + theta(s_{k-1}) dt/2 [k > 0],
 //                 Z at s_k for k < N (the last group is the trailing X half-step)
-__device__ inline void dev_op_angles(const RecGeom &G, const DevCouplings &c, const double *__restrict__ sv,
-                                     int op, double *thx, double *zA, double *zB, bool *has_z) {
+//   path mode: step k uses H1 with couplings cpl[k * batch + b] (s = 1)
+__device__ inline void dev_op_angles(const RecGeom &G, const DevCouplings *__restrict__ cpl, int b,
+                                     const double *__restrict__ sv, int op, double *thx, double *zA, double *zB,
+                                     bool *has_z) {
     thx[0] = thx[1] = 0.0;
     *zA = *zB = 0.0;
     *has_z = false;
     const int N = G.n_steps;
+    auto cp = [&](int k) -> const DevCouplings & { return G.path ? cpl[(long long)k * G.batch + b] : cpl[b]; };
+    auto sk = [&](int k) -> double { return G.path ? 1.0 : sv[k]; };
     auto add = [&](int k, double tau) {
-        const double s = sv[k];
+        const double s = sk(k);
+        const DevCouplings &c = cp(k);
         thx[0] += ((1.0 - s) + s * c.g) * tau;
         thx[1] += ((1.0 - s) + s * c.J) * tau;
     };
+    auto zs = [&](int k) {
+        const double s = sk(k);
+        const DevCouplings &c = cp(k);
+        *zA = s * c.h * G.dt; *zB = s * c.lambda * G.dt; *has_z = true;
+    };
     if (!G.fsal) {
         add(op, G.dt);
-        *zA = sv[op] * c.h * G.dt; *zB = sv[op] * c.lambda * G.dt; *has_z = true;
+        zs(op);
     } else {
         if (op < N) add(op, 0.5 * G.dt);
         if (op > 0) add(op - 1, 0.5 * G.dt);
-        if (op < N) { *zA = sv[op] * c.h * G.dt; *zB = sv[op] * c.lambda * G.dt; *has_z = true; }
+        if (op < N) zs(op);
     }
 }
 
-// one thread per (op, batch, entry); entry 0 = X header, then Z table, then X table
+// one thread per (op, batch, entry); entry 0 = X header, then Z table, then X table;
+// records of ops op0 .. op0 + n_ops - 1 are written from recs[0]
 __global__ void k_build_records(RecGeom G, const DevCouplings *__restrict__ cpl, const double *__restrict__ sv,
-                                int n_ops, double *__restrict__ recs) {
+                                int op0, int n_ops, double *__restrict__ recs) {
     const int nz = (G.nA + 1) * (G.nB + 1);
     const int nx = G.xlut_off > 0 ? (G.nXA + 1) * (G.nXB + 1) : 0;
     const long long per = 1 + nz + nx;
@@ -561,10 +573,10 @@ __global__ void k_build_records(RecGeom G, const DevCouplings *__restrict__ cpl,
          id += (long long)gridDim.x * blockDim.x) {
         const long long ob = id / per;
         const int e = (int)(id - ob * per);
-        const int op = (int)(ob / G.batch), b = (int)(ob % G.batch);
+        const int op = op0 + (int)(ob / G.batch), b = (int)(ob % G.batch);
         double thx[2], zA, zB;
         bool has_z;
-        dev_op_angles(G, cpl[b], sv, op, thx, &zA, &zB, &has_z);
+        dev_op_angles(G, cpl, b, sv, op, thx, &zA, &zB, &has_z);
         double *r = recs + ob * G.rec_stride;
         if (e == 0) {
             dev_unit_pair(G.f32, thx[0], &r[0], &r[1]);
@@ -615,6 +627,42 @@ __global__ void k_finish_wide(const double *__restrict__ partials, int nblk, int
         double s = 0.0;
         for (int k = 0; k < nblk; ++k) s += partials[((long long)b * nblk + k) * nval + v];
         out[(long long)b * nval + v] = s;
+    }
+}
+
+}  // namespace qsim
+
+namespace qsim {
+
+// Toric-code initial states of Sec. IV (before normalisation): amplitude 1 where every
+// plaquette parity is even (psi_1: the B_p = +1 projection of |+>), and additionally both
+// Wilson-loop masks w0, w1 even (psi_1': the A_v = +1 projection of |0...0>, whose support
+// is the star-flip orbit of |0...0>, i.e. the configurations orthogonal to every closed
+// loop); 0 elsewhere.
+template <typename R>
+__global__ void k_init_even(typename C2<R>::T *__restrict__ psi, int n, long long state_stride,
+                            const uint32_t *__restrict__ colA, unsigned long long w0, unsigned long long w1) {
+    __shared__ uint2 tab[MAXBYTES * 256];
+    // parity table of the plaquette columns only
+    for (int e = threadIdx.x; e < ((n + 7) / 8) * 256; e += blockDim.x) {
+        int k = e >> 8, val = e & 255;
+        uint32_t a = 0;
+        for (int j = 0; j < 8; ++j) {
+            int q = 8 * k + j;
+            if (q < n && ((val >> j) & 1)) a ^= colA[q];
+        }
+        tab[e] = make_uint2(a, 0u);
+    }
+    __syncthreads();
+    psi += (long long)blockIdx.y * state_stride;
+    const int nbytes = (n + 7) / 8;
+    const long long dim = 1ll << n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < dim;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint2 p = parity_of(tab, i, nbytes);
+        const bool keep = p.x == 0 && !(__popcll((unsigned long long)i & w0) & 1) &&
+                          !(__popcll((unsigned long long)i & w1) & 1);
+        psi[i] = mk<R>(keep ? (R)1 : (R)0, (R)0);
     }
 }
 

@@ -98,6 +98,9 @@ struct qs_sim {
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_key[10] = {0};
     long long graph_launches = 0;
+    // operator-record inputs (couplings, schedule) on the device
+    double *d_in = nullptr; size_t d_in_cap = 0;
+    bool in_path = false; size_t in_ncpl = 0;
     // scan workspaces
     double *d_scan = nullptr; size_t scan_cap = 0;
     double *h_scan = nullptr; size_t h_scan_cap = 0;
@@ -336,15 +339,26 @@ void unit_pair(bool f32, double t, double *ou, double *os) {
     *ou = bu; *os = bs;
 }
 
-// ops[k * batch + b]
-std::vector<Op> build_ops(const qs_couplings *c, int batch, const double *sv, double dt,
-                          int n_steps, int order, bool fsal) {
+// ops[k * batch + b].  path: step k uses H1 with couplings c[k * batch + b] (s = 1);
+// otherwise H(s_k) with couplings c[b].
+std::vector<Op> build_ops(const qs_couplings *c0, int batch, const double *sv0, double dt,
+                          int n_steps, int order, bool fsal, bool path = false) {
     std::vector<Op> ops;
+    std::vector<double> ones;
+    if (path) ones.assign(n_steps, 1.0);
+    const double *sv = path ? ones.data() : sv0;
+    int kcur = 0;   // step whose couplings `c` points at (path mode)
+    auto cpl = [&](int b) -> const qs_couplings & { return path ? c0[(size_t)kcur * batch + b] : c0[b]; };
     auto xang = [&](int b, double sk, double tau, double *out) {
-        Coef q = coefficients(c[b], sk);
+        Coef q = coefficients(cpl(b), sk);
         out[0] = q.xs * tau; out[1] = q.xt * tau;
     };
+    struct CView {
+        decltype(cpl) &f;
+        const qs_couplings &operator[](int b) const { return f(b); }
+    } c{cpl};
     for (int k = 0; k < n_steps; ++k) {
+        kcur = k;
         if (order == 1) {
             for (int b = 0; b < batch; ++b) {
                 Op o{}; xang(b, sv[k], dt, o.thx);
@@ -356,8 +370,9 @@ std::vector<Op> build_ops(const qs_couplings *c, int batch, const double *sv, do
             for (int b = 0; b < batch; ++b) {
                 Op o{};
                 double a[2], p[2] = {0.0, 0.0};
+                kcur = k;
                 xang(b, sv[k], 0.5 * dt, a);
-                if (k > 0) xang(b, sv[k - 1], 0.5 * dt, p);
+                if (k > 0) { kcur = k - 1; xang(b, sv[k - 1], 0.5 * dt, p); kcur = k; }
                 o.thx[0] = a[0] + p[0]; o.thx[1] = a[1] + p[1];
                 Coef q = coefficients(c[b], sv[k]);
                 o.zA = q.za * dt; o.zB = q.zb * dt; o.has_z = true;
@@ -612,13 +627,30 @@ qs_status renormalise(qs_sim *s) {
     return QS_OK;
 }
 
-// Operator records for the fused path, built on the device by k_build_records from
-// the couplings and the schedule (the only host->device bytes per call).
-qs_status upload_records(qs_sim *s, size_t n_ops, const qs_couplings *c, const double *sv, double dt,
-                         int n_steps, int order) {
+template <typename T>
+qs_status grow(qs_sim *s, T **p, size_t *cap, size_t need, bool host) {
+    if (need <= *cap) return QS_OK;
+    if (*p) {
+        if (host) cudaFreeHost(*p);
+        else { CK(s, cudaStreamSynchronize(s->stream)); cudaFree(*p); }
+    }
+    *p = nullptr; *cap = 0;
+    cudaError_t e = host ? cudaMallocHost((void **)p, need * sizeof(T)) : cudaMalloc((void **)p, need * sizeof(T));
+    if (e != cudaSuccess) FAIL(s, QS_ERR_OOM, "workspace of %zu elements", need);
+    *cap = need;
+    return QS_OK;
+}
+
+// Operator records for the fused path are built on the device by k_build_records
+// from the couplings and the schedule: upload_inputs copies those (the only
+// host->device bytes of a call) and build_records fills the records of ops
+// [op0, op0 + n) into d_rec.
+constexpr size_t REC_CHUNK = 2048;   // ops whose records are resident at once
+
+qs_status upload_inputs(qs_sim *s, const qs_couplings *c, const double *sv, int n_steps, bool path) {
     const int B = s->batch;
-    size_t need = n_ops * B * (size_t)s->rec_stride;
-    size_t in_doubles = (size_t)B * 4 + (size_t)n_steps;
+    const size_t ncpl = (size_t)B * (path ? n_steps : 1);
+    const size_t in_doubles = ncpl * 4 + (path ? 0 : (size_t)n_steps);
     if (s->rec_pending) {
         CK(s, cudaEventSynchronize(s->rec_done));
         s->rec_pending = false;
@@ -631,49 +663,52 @@ qs_status upload_records(qs_sim *s, size_t n_ops, const qs_couplings *c, const d
             FAIL(s, QS_ERR_OOM, "pinned schedule buffer (%zu doubles)", in_doubles);
         s->h_rec_cap = in_doubles;
     }
-    if (need + in_doubles > s->d_rec_cap) {
-        // the previous device buffer may still be read by queued kernels
-        if (s->d_rec) { CK(s, cudaStreamSynchronize(s->stream)); cudaFree(s->d_rec); }
-        s->d_rec = nullptr;
-        s->d_rec_cap = 0;
-        if (cudaMalloc((void **)&s->d_rec, (need + in_doubles) * sizeof(double)) != cudaSuccess)
-            FAIL(s, QS_ERR_OOM, "device record buffer (%zu doubles)", need);
-        s->d_rec_cap = need + in_doubles;
+    qs_status st;
+    if ((st = grow(s, &s->d_in, &s->d_in_cap, in_doubles, false)) != QS_OK) return st;
+    for (size_t i = 0; i < ncpl; ++i) {
+        s->h_rec[4 * i + 0] = c[i].J; s->h_rec[4 * i + 1] = c[i].h;
+        s->h_rec[4 * i + 2] = c[i].g; s->h_rec[4 * i + 3] = c[i].lambda;
     }
-    for (int b = 0; b < B; ++b) {
-        s->h_rec[4 * b + 0] = c[b].J; s->h_rec[4 * b + 1] = c[b].h;
-        s->h_rec[4 * b + 2] = c[b].g; s->h_rec[4 * b + 3] = c[b].lambda;
-    }
-    memcpy(s->h_rec + 4 * B, sv, (size_t)n_steps * sizeof(double));
-    double *d_in = s->d_rec + need;     // inputs live after the records
-    CK(s, cudaMemcpyAsync(d_in, s->h_rec, in_doubles * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+    if (!path) memcpy(s->h_rec + 4 * ncpl, sv, (size_t)n_steps * sizeof(double));
+    CK(s, cudaMemcpyAsync(s->d_in, s->h_rec, in_doubles * sizeof(double), cudaMemcpyHostToDevice, s->stream));
     CK(s, cudaEventRecord(s->rec_done, s->stream));
     s->rec_pending = true;
+    s->in_path = path;
+    s->in_ncpl = ncpl;
+    return QS_OK;
+}
+
+qs_status build_records(qs_sim *s, size_t op0, size_t n, double dt, int n_steps, int order) {
+    const int B = s->batch;
+    qs_status st;
+    if ((st = grow(s, &s->d_rec, &s->d_rec_cap, n * B * (size_t)s->rec_stride, false)) != QS_OK) return st;
     RecGeom G;
-    G.n_steps = n_steps; G.order = order; G.fsal = (order == 2);
+    G.n_steps = n_steps; G.order = order; G.fsal = (order == 2); G.path = s->in_path ? 1 : 0;
     G.batch = B; G.rec_stride = s->rec_stride;
     G.nA = s->nA; G.nB = s->nB; G.nXA = s->nXA; G.nXB = s->nXB;
     G.xlut_off = s->lat.gauge_higgs ? 0 : s->xlut_off;
     G.f32 = s->dtype == QS_C64;
     G.dt = dt;
-    long long entries = (long long)n_ops * B * (1 + (s->nA + 1) * (s->nB + 1) +
-                                               (G.xlut_off ? (s->nXA + 1) * (s->nXB + 1) : 0));
+    long long entries = (long long)n * B * (1 + (s->nA + 1) * (s->nB + 1) +
+                                            (G.xlut_off ? (s->nXA + 1) * (s->nXB + 1) : 0));
     unsigned blocks = (unsigned)std::min<long long>((entries + 255) / 256, 152 * 16);
-    k_build_records<<<blocks, 256, 0, s->stream>>>(G, reinterpret_cast<const DevCouplings *>(d_in), d_in + 4 * B,
-                                                   (int)n_ops, s->d_rec);
+    k_build_records<<<blocks, 256, 0, s->stream>>>(G, reinterpret_cast<const DevCouplings *>(s->d_in),
+                                                   s->d_in + 4 * s->in_ncpl, (int)op0, (int)n, s->d_rec);
     CKL(s);
     s->launches++;
     return QS_OK;
 }
 
 template <typename R>
-qs_status launch_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit) {
+qs_status launch_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit, size_t j0 = 0,
+                     size_t j1 = (size_t)-1) {
     qs_status st;
     const int B = s->batch;
     const size_t nops = ops.size() / B;
-    for (size_t k = 0; k < nops; ++k) {
+    if (j1 > nops) j1 = nops;
+    for (size_t k = j0; k < j1; ++k) {
         if (s->method == 0)
-            st = run_op_fused<R>(s, &ops[k * B], s->d_rec + k * B * (size_t)s->rec_stride, k, nops);
+            st = run_op_fused<R>(s, &ops[k * B], s->d_rec + (k - j0) * B * (size_t)s->rec_stride, k, nops);
         else
             st = run_op_pergate<R>(s, &ops[k * B]);
         if (st != QS_OK) return st;
@@ -686,12 +721,23 @@ qs_status launch_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm
 
 template <typename R>
 qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit, const qs_couplings *c,
-                  const double *sv, double dt, int n_steps, int order) {
+                  const double *sv, double dt, int n_steps, int order, bool path = false) {
     qs_status st;
     const int B = s->batch;
     const size_t nops = ops.size() / B;
-    if (s->method == 0)
-        if ((st = upload_records(s, nops, c, sv, dt, n_steps, order)) != QS_OK) return st;
+    if (s->method == 0) {
+        if ((st = upload_inputs(s, c, sv, n_steps, path)) != QS_OK) return st;
+        if (nops > REC_CHUNK) {
+            // long schedules: records of REC_CHUNK ops at a time, direct launches
+            for (size_t j0 = 0; j0 < nops; j0 += REC_CHUNK) {
+                const size_t j1 = std::min(nops, j0 + REC_CHUNK);
+                if ((st = build_records(s, j0, j1 - j0, dt, n_steps, order)) != QS_OK) return st;
+                if ((st = launch_ops<R>(s, ops, steps_per_renorm_unit, j0, j1)) != QS_OK) return st;
+            }
+            return QS_OK;
+        }
+        if ((st = build_records(s, 0, nops, dt, n_steps, order)) != QS_OK) return st;
+    }
     if (!s->use_graph || s->profile) return launch_ops<R>(s, ops, steps_per_renorm_unit);
     // Replay the launch sequence as a CUDA graph, captured once per configuration on a
     // private stream; the records it reads are rebuilt in place before every replay.
@@ -726,19 +772,6 @@ qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_un
 // ---------------------------------------------------------------------------
 // adjoint gradient
 // ---------------------------------------------------------------------------
-template <typename T>
-qs_status grow(qs_sim *s, T **p, size_t *cap, size_t need, bool host) {
-    if (need <= *cap) return QS_OK;
-    if (*p) {
-        if (host) cudaFreeHost(*p);
-        else { CK(s, cudaStreamSynchronize(s->stream)); cudaFree(*p); }
-    }
-    *p = nullptr; *cap = 0;
-    cudaError_t e = host ? cudaMallocHost((void **)p, need * sizeof(T)) : cudaMalloc((void **)p, need * sizeof(T));
-    if (e != cudaSuccess) FAIL(s, QS_ERR_OOM, "workspace of %zu elements", need);
-    *cap = need;
-    return QS_OK;
-}
 
 template <typename R>
 qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, double dt, int n_steps, int order,
@@ -795,8 +828,16 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
     if ((st = grow(s, &s->d_adj_part, &s->adj_part_cap, nblk * B * RED_NV, false)) != QS_OK) return st;
     if ((st = grow(s, &s->d_grad, &s->grad_cap, nops * B * RED_NV, false)) != QS_OK) return st;
     if ((st = grow(s, &s->h_grad, &s->h_grad_cap, nops * B * RED_NV, true)) != QS_OK) return st;
+    size_t chunk0 = (size_t)-1;   // first op whose record is resident in d_rec
     for (size_t jj = nops; jj-- > 0;) {
-        const double *rec = s->d_rec + jj * B * (size_t)s->rec_stride;
+        if (chunk0 == (size_t)-1 || jj < chunk0) {
+            // (re)build the records of the chunk holding op jj (the forward left the last one)
+            const size_t c0 = (jj / REC_CHUNK) * REC_CHUNK;
+            const size_t c1 = std::min(nops, c0 + REC_CHUNK);
+            if ((st = build_records(s, c0, c1 - c0, dt, n_steps, order)) != QS_OK) return st;
+            chunk0 = c0;
+        }
+        const double *rec = s->d_rec + (jj - chunk0) * B * (size_t)s->rec_stride;
         for (int pi = 0; pi < np; ++pi) {
             const int p = np - 1 - pi;
             k_adj_xpass<R><<<dim3(G, B), NT, smem, s->stream>>>(psi, lam, s->dim, ntiles, rec, s->rec_stride,
@@ -959,6 +1000,7 @@ void qs_destroy(qs_sim *s) {
     cudaFree(s->d_grad);
     cudaFree(s->d_hrec);
     cudaFree(s->d_scan);
+    cudaFree(s->d_in);
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->h_scan) cudaFreeHost(s->h_scan);
@@ -1033,6 +1075,25 @@ qs_status qs_init_plus(qs_sim *s) {
     return QS_OK;
 }
 
+qs_status qs_init_toric(qs_sim *s, int which) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (s->lat.gauge_higgs) FAIL(s, QS_ERR_ARG, "toric-code initial states are defined in the unitary gauge");
+    if (which != 0 && which != 1) FAIL(s, QS_ERR_ARG, "which must be 0 (B_p = +1 from |+>) or 1 (A_v = +1 from |0>)");
+    // support: every plaquette even; for which = 1 also both Wilson loops even
+    uint64_t w0 = 0, w1 = 0;
+    if (which == 1 && s->lat.wilson.size() == 2) { w0 = s->lat.wilson[0]; w1 = s->lat.wilson[1]; }
+    dim3 grid(152 * 8, (unsigned)s->batch);
+    if (s->dtype == QS_C64)
+        k_init_even<float><<<grid, 256, 0, s->stream>>>((float2 *)s->state[0], s->n, s->dim, s->d_colA,
+                                                         (unsigned long long)w0, (unsigned long long)w1);
+    else
+        k_init_even<double><<<grid, 256, 0, s->stream>>>((double2 *)s->state[0], s->n, s->dim, s->d_colA,
+                                                          (unsigned long long)w0, (unsigned long long)w1);
+    CKL(s); s->launches++;
+    return s->dtype == QS_C64 ? renormalise<float>(s) : renormalise<double>(s);
+}
+
 qs_status qs_upload_state(qs_sim *s, const void *host, size_t bytes) {
     qs_status st;
     if ((st = check_ready(s)) != QS_OK) return st;
@@ -1052,19 +1113,23 @@ qs_status qs_download_state(qs_sim *s, void *host, size_t bytes) {
 }
 
 static qs_status evolve_impl(qs_sim *s, const qs_couplings *c, const double *sv, double dt, int n_steps,
-                             int order) {
+                             int order, bool path = false) {
     qs_status st;
     if ((st = check_ready(s)) != QS_OK) return st;
-    if (!c || !sv) FAIL(s, QS_ERR_ARG, "null couplings or schedule");
+    if (!c || (!sv && !path)) FAIL(s, QS_ERR_ARG, "null couplings or schedule");
     if (order != 1 && order != 2) FAIL(s, QS_ERR_ARG, "order must be 1 or 2");
     if (n_steps < 0) FAIL(s, QS_ERR_ARG, "n_steps < 0");
     if (!std::isfinite(dt)) FAIL(s, QS_ERR_ARG, "dt not finite");
     if (n_steps == 0) return QS_OK;
     bool fsal = (s->method == 0);
-    std::vector<Op> ops = build_ops(c, s->batch, sv, dt, n_steps, order, fsal);
+    std::vector<Op> ops = build_ops(c, s->batch, sv, dt, n_steps, order, fsal, path);
     int per_step = (order == 2 && !fsal) ? 2 : 1;
-    if (s->dtype == QS_C64) return run_ops<float>(s, ops, per_step, c, sv, dt, n_steps, order);
-    return run_ops<double>(s, ops, per_step, c, sv, dt, n_steps, order);
+    if (s->dtype == QS_C64) return run_ops<float>(s, ops, per_step, c, sv, dt, n_steps, order, path);
+    return run_ops<double>(s, ops, per_step, c, sv, dt, n_steps, order, path);
+}
+
+qs_status qs_evolve_path(qs_sim *s, const qs_couplings *per_step, double dt, int n_steps, int order) {
+    return evolve_impl(s, per_step, nullptr, dt, n_steps, order, true);
 }
 
 qs_status qs_trotter_step(qs_sim *s, const qs_couplings *c, double sv, double dt, int order) {

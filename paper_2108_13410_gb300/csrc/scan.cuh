@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(NT, 2) k_scan12(const DevCouplings *__restrict
             __syncthreads();   // previous op's tables and tile writes are done
             double thx[2], zA, zB;
             bool has_z;
-            dev_op_angles(P.G, c, sv, op, thx, &zA, &zB, &has_z);
+            dev_op_angles(P.G, &c, 0, sv, op, thx, &zA, &zB, &has_z);
             if (t < 2) {
                 double u, s;
                 dev_unit_pair(sizeof(R) == 4, thx[t], &u, &s);

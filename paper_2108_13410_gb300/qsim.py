@@ -56,6 +56,8 @@ _SIGS = {
     "qs_set_stream": ([_P, _P], _I),
     "qs_set_option": ([_P, _I, _LL], _I),
     "qs_init_plus": ([_P], _I),
+    "qs_init_toric": ([_P, _I], _I),
+    "qs_evolve_path": ([_P, _CP, _D, _I, _I], _I),
     "qs_upload_state": ([_P, _P, _SZ], _I),
     "qs_download_state": ([_P, _P, _SZ], _I),
     "qs_trotter_step": ([_P, _CP, _D, _D, _I], _I),
@@ -165,6 +167,25 @@ def qs_set_option(sim, key: int, value: int):
 
 def qs_init_plus(sim):
     _check(sim, library().qs_init_plus(sim))
+
+
+def qs_init_toric(sim, which: int):
+    _check(sim, library().qs_init_toric(sim, which))
+
+
+def qs_evolve_path(sim, per_step, dt: float, order: int, batch: int = 1):
+    """per_step: sequence of n_steps coupling records (batch 1) or of n_steps lists of
+    `batch` records; step k evolves under H1 with those couplings."""
+    flat = []
+    for rec in per_step:
+        if batch == 1:
+            flat.append(rec)
+        else:
+            assert len(rec) == batch
+            flat.extend(rec)
+    n_steps = len(flat) // batch
+    arr = _couplings(flat, len(flat))
+    _check(sim, library().qs_evolve_path(sim, arr, dt, n_steps, order))
 
 
 def qs_upload_state(sim, host_ptr: int, nbytes: int):
@@ -342,6 +363,12 @@ class Simulator:
     # --- evolution ---
     def init_plus(self):
         qs_init_plus(self.h)
+
+    def init_toric(self, which=0):
+        qs_init_toric(self.h, which)
+
+    def evolve_path(self, per_step, dt, order=2):
+        qs_evolve_path(self.h, per_step, dt, order, self.batch)
 
     def trotter_step(self, couplings, s, dt, order=2):
         qs_trotter_step(self.h, couplings, s, dt, order, self.batch)

@@ -1,0 +1,80 @@
+"""Toric-code initial states (qs_init_toric) and parameter paths (qs_evolve_path) on the
+GPU against the oracle, including schedules longer than one chunk of operator records,
+and the adjoint over such a schedule."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import OracleLattice, Couplings
+from oracle import core as O
+
+gpu = pytest.mark.gpu
+
+
+def _sim(*a, **k):
+    from paper_2108_13410_gb300 import Simulator
+    return Simulator(*a, **k)
+
+
+def _close(got, ref, dtype):
+    tol = 1e-10 if dtype == "c128" else 1e-5
+    got = np.asarray(got, dtype=np.complex128)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= tol
+
+
+@gpu
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("L", [(3, 2), (3, 3)])
+def test_toric_initial_states(dtype, L):
+    lat = OracleLattice(L[0], L[1], True, "ug")
+    sim = _sim(L[0], L[1], form="ug", dtype=dtype)
+    for which in (0, 1):
+        sim.init_toric(which)
+        _close(sim.download()[0].numpy(), O.toric_state(lat, which), dtype)
+
+
+@gpu
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_path_longer_than_a_record_chunk(dtype):
+    """2500 steps (more than the 2048 operator records kept at once) of the blue path
+    on the 3x2 torus, unitary gauge, from psi_1."""
+    from paper_2108_13410_gb300.protocol import blue
+    lat = OracleLattice(3, 2, True, "ug")
+    path = blue(0.5, 0.5 / 2500)
+    assert len(path) == 2500
+    ref = O.evolve_path(lat, [Couplings(g, l, J=J, h=h) for g, l, J, h in path], 0.02, 2,
+                        psi0=O.toric_state(lat, 0))
+    sim = _sim(3, 2, form="ug", dtype=dtype)
+    sim.init_toric(0)
+    sim.evolve_path(path, 0.02, 2)
+    _close(sim.download()[0].numpy(), ref, dtype)
+    e = sim.energy([path[-1]])[0]
+    g, l, J, h = path[-1]
+    assert abs(e - O.energy(ref, lat, Couplings(g, l, J=J, h=h))) <= (1e-9 if dtype == "c128" else 1e-3)
+
+
+@gpu
+def test_gauge_higgs_path_matches_oracle():
+    lat = OracleLattice(3, 2, True, "gh")
+    path = [(0.1 + 0.01 * k, 0.3 - 0.005 * k, 0.8, 1.1) for k in range(40)]
+    ref = O.evolve_path(lat, [Couplings(g, l, J=J, h=h) for g, l, J, h in path], 0.05, 2)
+    sim = _sim(3, 2, form="gh", dtype="c128")
+    sim.init_plus()
+    sim.evolve_path(path, 0.05, 2)
+    _close(sim.download()[0].numpy(), ref, "c128")
+
+
+@gpu
+def test_adjoint_over_more_than_one_record_chunk():
+    lat = OracleLattice(2, 2, True, "gh")
+    c = Couplings(0.6, 0.6)
+    T, n, M = 21.0, 2100, 3
+    a = synth.fourier_coeffs(M, seed=4, std=0.05)
+    s = O.schedule_fourier(T, n, a)
+    jac = O.schedule_fourier_jacobian(T, n, M)
+    e_ref, g_ref = O.energy_gradient(lat, c, s, T / n, 2, jac)
+    sim = _sim(2, 2, form="gh", dtype="c128", aux=True)
+    sim.init_plus()
+    val, g = sim.adjoint_grad([(0.6, 0.6)], s, T / n, 2)
+    assert abs(val[0] - e_ref) <= 1e-9
+    np.testing.assert_allclose(jac @ g[0], g_ref, atol=1e-8 * np.max(np.abs(g_ref)) + 1e-12)
