@@ -1,0 +1,263 @@
+// adjoint_tma.cuh -- persistent, TMA-fed reverse pass of the adjoint gradient (complex64).
+//
+// The reverse sweep of adjoint.cuh with both states streamed by TMA: each tile buffer
+// holds the psi tile and the lambda tile (two 5-D tensor-map loads, one mbarrier).  The
+// sweep runs in the real-rotation frame phi = i^popc psi (both states converted on the
+// first reverse pass, psi converted back on the last), where the inverse factor is the
+// real rotation [[c, -s], [s, c]] (packed FP32x2 FMAs) and the X-group derivative term
+//     Im<lambda|X_q|psi> = Im<lambda_phi|Y_q|psi_phi> = sum_pairs Re(conj(l_b) p_a) - Re(conj(l_a) p_b).
+// The first reverse pass of a factor group undoes the Z layer in stage A (before any
+// X term of the group is read) and accumulates the Z-group terms
+//     Im(conj(lambda_i) psi_i) (nA - 2 oddA(i)),  ... (nB - 2 oddB(i)).
+#pragma once
+#include "xpass_tma.cuh"
+
+namespace qsim {
+
+__device__ __forceinline__ float rdot(u64 a, u64 b) {   // Re(conj(a) b) for packed complex
+    const float2 x = unpk(a), y = unpk(b);
+    return x.x * y.x + x.y * y.y;
+}
+
+__device__ __forceinline__ float idot(u64 l, u64 p) {   // Im(conj(l) p)
+    const float2 x = unpk(l), y = unpk(p);
+    return x.x * y.y - x.y * y.x;
+}
+
+// reverse real-frame rotations on psi and lambda with the X-group terms read first
+__device__ __forceinline__ void adj_rotate_w(u64 (&p)[NR], u64 (&l)[NR], unsigned mask, const int (&cls)[RB],
+                                             const RotConst &C, float &g0, float &g1) {
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+        const bool c = cls[k] != 0;
+        // inverse rotation: s -> -s
+        const u64 nu = c ? C.nu[1] : C.nu[0], ps = c ? C.ns[1] : C.ns[0], ns = c ? C.ps[1] : C.ps[0];
+        float g = 0.f;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if ((r >> k) & 1) continue;
+            const int q = r | (1 << k);
+            g += rdot(l[q], p[r]) - rdot(l[r], p[q]);
+            rrotp(p[r], p[q], nu, ps, ns);
+            rrotp(l[r], l[q], nu, ps, ns);
+        }
+        if (c) g1 += g; else g0 += g;
+    }
+}
+
+template <int NBUF>
+__global__ void __launch_bounds__(NT, 1) k_adj_tma(float2 *__restrict__ psi, float2 *__restrict__ lam,
+                                                   const double *__restrict__ recs, int rec_stride, int tiles_shift,
+                                                   int *__restrict__ err_flag, double *__restrict__ partials,
+                                                   int nblk, int slot0, int zinv,
+                                                   const __grid_constant__ CUtensorMap tmap_p,
+                                                   const __grid_constant__ CUtensorMap tmap_l,
+                                                   const __grid_constant__ TmaPass P) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base_ptr = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    float2 *buf = reinterpret_cast<float2 *>(base_ptr);                       // NBUF x (psi, lambda) tiles
+    float2 *lut = buf + 2 * NBUF * (1 << LT);
+    uint2 *ptab = reinterpret_cast<uint2 *>(lut + (P.nA + 1) * (P.nB + 1));  // 3 x 256
+    __shared__ uint64_t bars[NBUF];
+    __shared__ int s_ok;
+    __shared__ double red[NT / 32][4];
+
+    const int t = threadIdx.x;
+    const long long G = gridDim.x;
+    const long long T = P.total_tiles;
+    const long long first = blockIdx.x;
+    const long long max_wait = 2000000000ll;
+
+    if (t == 0) {
+        for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
+    }
+    for (int e = t; e < 3 * 256; e += NT) {
+        int byte = e >> 8, val = e & 255;
+        uint32_t a = 0, b = 0;
+        for (int j = 0; j < 8; ++j) {
+            int bit = 8 * byte + j;
+            if (bit < P.tile_bits && ((val >> j) & 1)) { a ^= P.pa_tile[bit]; b ^= P.pb_tile[bit]; }
+        }
+        ptab[e] = make_uint2(a, b);
+    }
+    __syncthreads();
+
+    auto issue = [&](int it) {
+        long long tile = first + (long long)it * G;
+        int b = it % NBUF;
+        int x2 = (int)(tile & ((1ll << P.mid_bits) - 1));
+        int x4 = (int)(tile >> P.mid_bits);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive_expect_tx(&bars[b], 2 * TMA_TILE_BYTES);
+        tma_load_5d(buf + (size_t)(2 * b) * (1 << LT), &tmap_p, &bars[b], 0, 0, x2, 0, x4);
+        tma_load_5d(buf + (size_t)(2 * b + 1) * (1 << LT), &tmap_l, &bars[b], 0, 0, x2, 0, x4);
+    };
+    const int n_my = first < T ? (int)((T - first + G - 1) / G) : 0;
+    if (t == 0)
+        for (int it = 0; it < NBUF - 1 && it < n_my; ++it) issue(it);
+
+    const int tlo = t & 15, thi = t >> 4;
+    const int a_base = swz128(t);
+    int c_base[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) c_base[j] = (tlo ^ (j << 1)) | (thi << 8);
+    const int b_base = t << 3, b_x = t & 7;
+    long long toff = 0;
+    uint32_t paA_t = 0, pbA_t = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if ((tlo >> j) & 1) toff += P.toff_c[j];
+        if ((thi >> j) & 1) toff += P.toff_c[4 + j];
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if ((t >> j) & 1) { paA_t ^= P.paA_thr[j]; pbA_t ^= P.pbA_thr[j]; }
+    const int nB1 = P.nB + 1, nlut = (P.nA + 1) * nB1;
+    int cls0[RB], cls1[RB], cls2[RB];
+#pragma unroll
+    for (int kk = 0; kk < RB; ++kk) {
+        cls0[kk] = (P.cls[0] >> kk) & 1; cls1[kk] = (P.cls[1] >> kk) & 1; cls2[kk] = (P.cls[2] >> kk) & 1;
+    }
+    const long long tmask = (1ll << tiles_shift) - 1;
+    long long cur_batch = -1;
+    RotConst RC;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+
+    long long tile = first;
+    for (int it = 0; it < n_my; ++it, tile += G) {
+        const int b = it % NBUF;
+        const uint32_t parity = (uint32_t)((it / NBUF) & 1);
+        const long long batch = tile >> tiles_shift;
+        if (batch != cur_batch) {
+            if (cur_batch >= 0) {
+                // flush the previous batch element's sums
+                __syncthreads();
+                for (int v = 0; v < 4; ++v) {
+                    double x = warp_sum(acc[v]);
+                    if ((t & 31) == 0) red[t >> 5][v] = x;
+                }
+                __syncthreads();
+                if (t < 4) {
+                    double sum = 0.0;
+                    for (int w = 0; w < NT / 32; ++w) sum += red[w][t];
+                    partials[(cur_batch * nblk + slot0 + blockIdx.x) * RED_NV + t] = sum;
+                }
+                acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
+            }
+            __syncthreads();
+            const double *rec = recs + batch * rec_stride;
+            const float u0 = (float)rec[0], s0 = (float)rec[1], u1 = (float)rec[2], s1 = (float)rec[3];
+            RC.nu[0] = pk(-u0, -u0); RC.ps[0] = pk(s0, s0); RC.ns[0] = pk(-s0, -s0);
+            RC.nu[1] = pk(-u1, -u1); RC.ps[1] = pk(s1, s1); RC.ns[1] = pk(-s1, -s1);
+            if (zinv)   // inverse Z layer: conjugated phase table
+                for (int i = t; i < nlut; i += NT) lut[i] = make_float2((float)rec[4 + 2 * i], -(float)rec[5 + 2 * i]);
+            cur_batch = batch;
+        }
+        if (t == 0) {
+            if (!mbar_wait_bounded(&bars[b], parity, max_wait)) {
+                atomicOr(err_flag, 1);
+                s_ok = 0;
+                for (int j = it; j < it + NBUF - 1 && j < n_my; ++j)
+                    mbar_wait_bounded(&bars[j % NBUF], (uint32_t)((j / NBUF) & 1), max_wait);
+            }
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        if (t == 0 && it + NBUF - 1 < n_my) issue(it + NBUF - 1);
+
+        u64 *tp = reinterpret_cast<u64 *>(buf + (size_t)(2 * b) * (1 << LT));
+        u64 *tl = reinterpret_cast<u64 *>(buf + (size_t)(2 * b + 1) * (1 << LT));
+        u64 p[NR], l[NR];
+        float g0 = 0.f, g1 = 0.f, ga = 0.f, gb = 0.f;
+        const long long tin = tile & tmask;
+        const int pc_tile = __popcll(tin);
+        // ---- stage A ----
+#pragma unroll
+        for (int r = 0; r < NR; ++r) { p[r] = tp[a_base + (r << TB)]; l[r] = tl[a_base + (r << TB)]; }
+        if (zinv) {
+            const uint2 e0 = ptab[tin & 255], e1 = ptab[256 + ((tin >> 8) & 255)], e2 = ptab[512 + ((tin >> 16) & 255)];
+            const uint32_t pa = paA_t ^ e0.x ^ e1.x ^ e2.x, pb = pbA_t ^ e0.y ^ e1.y ^ e2.y;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int oa = __popc(pa ^ P.paA_reg[r]), ob = __popc(pb ^ P.pbA_reg[r]);
+                const float im = idot(l[r], p[r]);
+                ga += im * (float)(P.nA - 2 * oa);
+                gb += im * (float)(P.nB - 2 * ob);
+                const float2 ph = lut[oa * nB1 + ob];
+                const float2 vp = cphase(unpk(p[r]), ph), vl = cphase(unpk(l[r]), ph);
+                p[r] = pk(vp.x, vp.y);
+                l[r] = pk(vl.x, vl.y);
+            }
+        }
+        if (P.frame & 2) {
+            const int k0 = __popc(t) + pc_tile;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float2 vp = mul_ipow(unpk(p[r]), k0 + __popc(r)), vl = mul_ipow(unpk(l[r]), k0 + __popc(r));
+                p[r] = pk(vp.x, vp.y);
+                l[r] = pk(vl.x, vl.y);
+            }
+        }
+        adj_rotate_w(p, l, P.rot[0], cls0, RC, g0, g1);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) { tp[a_base + (r << TB)] = p[r]; tl[a_base + (r << TB)] = l[r]; }
+        __syncthreads();
+        // ---- stage B ----
+        if (P.stage_b) {
+            ulonglong2 *tp2 = reinterpret_cast<ulonglong2 *>(tp), *tl2 = reinterpret_cast<ulonglong2 *>(tl);
+#pragma unroll
+            for (int m = 0; m < NR / 2; ++m) {
+                const ulonglong2 qp = tp2[b_base + (m ^ b_x)], ql = tl2[b_base + (m ^ b_x)];
+                p[2 * m] = qp.x; p[2 * m + 1] = qp.y;
+                l[2 * m] = ql.x; l[2 * m + 1] = ql.y;
+            }
+            adj_rotate_w(p, l, P.rot[1], cls1, RC, g0, g1);
+#pragma unroll
+            for (int m = 0; m < NR / 2; ++m) {
+                tp2[b_base + (m ^ b_x)] = make_ulonglong2(p[2 * m], p[2 * m + 1]);
+                tl2[b_base + (m ^ b_x)] = make_ulonglong2(l[2 * m], l[2 * m + 1]);
+            }
+            __syncthreads();
+        }
+        // ---- stage C ----
+#pragma unroll
+        for (int r = 0; r < NR; ++r) { p[r] = tp[c_base[r & 7] + (r << 4)]; l[r] = tl[c_base[r & 7] + (r << 4)]; }
+        adj_rotate_w(p, l, P.rot[2], cls2, RC, g0, g1);
+        if (P.frame & 4) {
+            const int k0 = -(__popc(tlo) + __popc(thi) + pc_tile);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int kk = (k0 - __popc(r)) & 3;
+                const float2 vp = mul_ipow(unpk(p[r]), kk), vl = mul_ipow(unpk(l[r]), kk);
+                p[r] = pk(vp.x, vp.y);
+                l[r] = pk(vl.x, vl.y);
+            }
+        }
+        const long long mid = tile & ((1ll << P.mid_bits) - 1);
+        const long long up = tile >> P.mid_bits;
+        const long long gbase = (mid << P.c) + (up << (P.next + P.k)) + toff;
+        u64 *dp = reinterpret_cast<u64 *>(psi + gbase);
+        u64 *dl = reinterpret_cast<u64 *>(lam + gbase);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) { dp[P.roff_c[r]] = p[r]; dl[P.roff_c[r]] = l[r]; }
+        acc[0] += (double)g0; acc[1] += (double)g1; acc[2] += (double)ga; acc[3] += (double)gb;
+    }
+    // flush the last batch element's sums
+    __syncthreads();
+    for (int v = 0; v < 4; ++v) {
+        double x = warp_sum(acc[v]);
+        if ((t & 31) == 0) red[t >> 5][v] = x;
+    }
+    __syncthreads();
+    if (t < 4 && cur_batch >= 0) {
+        double sum = 0.0;
+        for (int w = 0; w < NT / 32; ++w) sum += red[w][t];
+        partials[(cur_batch * nblk + slot0 + blockIdx.x) * RED_NV + t] = sum;
+    }
+}
+
+}  // namespace qsim

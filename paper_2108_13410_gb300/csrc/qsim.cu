@@ -19,6 +19,7 @@
 #include "kernels.cuh"
 #include "xpass_tma.cuh"
 #include "adjoint.cuh"
+#include "adjoint_tma.cuh"
 #include "scan.cuh"
 
 using namespace qsim;
@@ -87,6 +88,8 @@ struct qs_sim {
     std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
     std::vector<CUtensorMap> tmaps;        // one per pass, encoded for the bound state
     bool tmaps_ok = false;
+    std::vector<CUtensorMap> tmaps_aux;    // the same over the adjoint work state (slot 1)
+    bool tmaps_aux_ok = false;
     int *d_err = nullptr;                  // device flag: bounded wait gave up
     // adjoint workspaces
     double *d_adj_part = nullptr; size_t adj_part_cap = 0;
@@ -242,6 +245,13 @@ void build_tma_passes(qs_sim *s) {
                 if ((r >> kk) & 1) { int q = g(4 + kk); off += 1ll << q; a ^= d.colA[q]; b ^= d.colB[q]; }
             P.roff_c[r] = off; P.pa_reg[r] = a; P.pb_reg[r] = b;
         }
+        for (int j = 0; j < 8; ++j) { int q = g(j); P.paA_thr[j] = d.colA[q]; P.pbA_thr[j] = d.colB[q]; }
+        for (int r = 0; r < NR; ++r) {
+            uint32_t a = 0, b = 0;
+            for (int kk = 0; kk < RB; ++kk)
+                if ((r >> kk) & 1) { int q = g(8 + kk); a ^= d.colA[q]; b ^= d.colB[q]; }
+            P.paA_reg[r] = a; P.pbA_reg[r] = b;
+        }
         const int stage_base[3] = {8, 0, 4};
         for (int st = 0; st < 3; ++st) {
             unsigned cl = 0;
@@ -268,10 +278,12 @@ void build_tma_passes(qs_sim *s) {
 // Encode one 5-D tensor map per pass over the bound complex64 state:
 //   dims (8-byte elements) {16, 2^(c-4), 2^(next-c), 2^k, 2^(n-next-k) * batch},
 //   box {16, 2^(c-4), 1, 2^k, 1}, 128-byte swizzle.
-qs_status encode_tmaps(qs_sim *s) {
-    s->tmaps_ok = false;
-    s->tmaps.clear();
-    if (s->dtype != QS_C64 || s->passes.empty() || !s->state[0]) return QS_OK;
+qs_status encode_tmaps(qs_sim *s, int slot = 0) {
+    std::vector<CUtensorMap> &maps = slot == 0 ? s->tmaps : s->tmaps_aux;
+    bool &ok = slot == 0 ? s->tmaps_ok : s->tmaps_aux_ok;
+    ok = false;
+    maps.clear();
+    if (s->dtype != QS_C64 || s->passes.empty() || !s->state[slot]) return QS_OK;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -290,13 +302,13 @@ qs_status encode_tmaps(qs_sim *s) {
         cuuint32_t box[5] = {16, (cuuint32_t)(1u << (P.c - 4)), 1, (cuuint32_t)(1u << P.k), 1};
         cuuint32_t es[5] = {1, 1, 1, 1, 1};
         CUtensorMap m;
-        CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, s->state[0], dims, strides, box, es,
+        CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, s->state[slot], dims, strides, box, es,
                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) FAIL(s, QS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for pass %zu", (int)r, p);
-        s->tmaps.push_back(m);
+        maps.push_back(m);
     }
-    s->tmaps_ok = true;
+    ok = true;
     return QS_OK;
 }
 
@@ -825,7 +837,18 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
     }
     // ---- reverse sweep ----
     const size_t nblk = (size_t)np * G;
-    if ((st = grow(s, &s->d_adj_part, &s->adj_part_cap, nblk * B * RED_NV, false)) != QS_OK) return st;
+    const bool use_tma = sizeof(R) == 4 && s->tmaps_ok && s->tmaps_aux_ok && s->xpass_impl != 1;
+    const size_t adj_smem = 2 * 2 * (size_t)TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8;
+    unsigned Gt = 1;
+    if (use_tma) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_tma<2>, NT, adj_smem);
+        if (per_sm < 1) per_sm = 1;
+        Gt = (unsigned)std::min<long long>((long long)B << (s->n - LT), (long long)per_sm * s->sm_count);
+    }
+    const size_t nblk_t = (size_t)np * Gt;
+    if ((st = grow(s, &s->d_adj_part, &s->adj_part_cap, std::max(nblk, nblk_t) * B * RED_NV, false)) != QS_OK)
+        return st;
     if ((st = grow(s, &s->d_grad, &s->grad_cap, nops * B * RED_NV, false)) != QS_OK) return st;
     if ((st = grow(s, &s->h_grad, &s->h_grad_cap, nops * B * RED_NV, true)) != QS_OK) return st;
     size_t chunk0 = (size_t)-1;   // first op whose record is resident in d_rec
@@ -838,6 +861,23 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
             chunk0 = c0;
         }
         const double *rec = s->d_rec + (jj - chunk0) * B * (size_t)s->rec_stride;
+        if (use_tma) {
+            CK(s, cudaMemsetAsync(s->d_adj_part, 0, nblk_t * B * RED_NV * sizeof(double), s->stream));
+            for (int pi = 0; pi < np; ++pi) {
+                const int p = np - 1 - pi;
+                TmaPass P = s->tpasses[NVAR * p + V_ROT];
+                P.frame = 1 | ((jj + 1 == nops && pi == 0) ? 2 : 0) | ((jj == 0 && pi == np - 1) ? 4 : 0);
+                const int zinv = (pi == 0 && ops[jj * B].has_z) ? 1 : 0;
+                k_adj_tma<2><<<Gt, NT, adj_smem, s->stream>>>((float2 *)s->state[0], (float2 *)s->state[1], rec,
+                                                            s->rec_stride, s->n - LT, s->d_err, s->d_adj_part,
+                                                            (int)nblk_t, pi * (int)Gt, zinv, s->tmaps[p],
+                                                            s->tmaps_aux[p], P);
+                CKL(s); s->launches++;
+            }
+            k_finish<<<B, RED_THREADS, 0, s->stream>>>(s->d_adj_part, (int)nblk_t, 4, s->d_grad + jj * B * RED_NV);
+            CKL(s); s->launches++;
+            continue;
+        }
         for (int pi = 0; pi < np; ++pi) {
             const int p = np - 1 - pi;
             k_adj_xpass<R><<<dim3(G, B), NT, smem, s->stream>>>(psi, lam, s->dim, ntiles, rec, s->rec_stride,
@@ -978,6 +1018,8 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
         cudaFuncSetAttribute(k_apply_h_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_apply_h_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_xmeasure<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1 << LT) * 16));
+        cudaFuncSetAttribute(k_adj_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(4 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
     }
     size_t smem64 = (size_t)(1 << LT) * 16 + (size_t)s->max_lut * 16;
     cudaFuncSetAttribute(k_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
@@ -1031,8 +1073,7 @@ qs_status qs_bind_state(qs_sim *s, int slot, void *ptr, size_t bytes) {
     if (bytes < qs_state_bytes(s)) FAIL(s, QS_ERR_ARG, "buffer of %zu bytes < %zu", bytes, qs_state_bytes(s));
     s->state[slot] = ptr;
     s->state_cap[slot] = bytes;
-    if (slot == 0) return encode_tmaps(s);
-    return QS_OK;
+    return encode_tmaps(s, slot);
 }
 
 qs_status qs_set_stream(qs_sim *s, void *stream) {

@@ -47,6 +47,8 @@ struct TmaPass {
     float scale;                // factor applied with the phase (a power of two)
     int frame;                  // bit 0: rotations in the frame phi_i = i^popc(i) psi_i;
                                 // bit 1: convert psi -> phi at stage A; bit 2: phi -> psi at stage C
+    uint32_t paA_thr[8], pbA_thr[8];  // parity columns of the stage-A thread bits (local 0..7)
+    uint32_t paA_reg[NR], pbA_reg[NR];// parity of stage-A register r (local bits 8..11)
 };
 
 constexpr int TMA_TILE_BYTES = (1 << LT) * 8;

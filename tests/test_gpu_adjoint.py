@@ -117,3 +117,23 @@ def test_adjoint_matches_finite_differences_on_the_gpu_path():
         fd.append((energy(a0 + d) - energy(a0 - d)) / (2 * h))
     fd = np.array(fd)
     assert np.max(np.abs(a.grad.numpy() - fd)) <= 1e-6 * max(1.0, np.max(np.abs(fd)))
+
+
+@gpu
+@pytest.mark.parametrize("L", [(2, 2), (3, 2)])
+def test_batched_complex64_adjoint_tma_path(L):
+    """complex64 adjoint (TMA reverse pass) with two batch elements: per-element sums."""
+    couplings = [(0.2, 0.9), (0.6, 0.6)]
+    T, n = 2.0, 12
+    s = O.schedule_linear(T, n)
+    sim = _sim(*L, form="gh", dtype="c64", batch=2, aux=True)
+    sim.init_plus()
+    val, g = sim.adjoint_grad(couplings, s, T / n, 2)
+    lat = OracleLattice(*L, True, "gh")
+    for b, (gg, lam) in enumerate(couplings):
+        e_ref, g_ref = O.energy_gradient(lat, Couplings(gg, lam), s, T / n, 2, np.eye(n))
+        assert abs(val[b] - e_ref) <= 1e-4 * abs(e_ref)
+        _close(g[b], g_ref, 1e-3)
+    psi0 = sim.download().numpy().astype(np.complex128)
+    for b in range(2):
+        assert np.linalg.norm(psi0[b] - O.plus_state(lat.n_qubits)) <= 1e-4
