@@ -88,8 +88,11 @@ typedef enum {
     QS_OPT_GRAPH = 3,         /* 1: qs_evolve replays its launches as a CUDA graph    */
     QS_OPT_XPASS = 4,         /* X-pass kernel for complex64: 0 auto (TMA), 1 the
                                  register-staged kernel, 2 the persistent TMA kernel */
-    QS_OPT_TMA_BUFFERS = 5    /* shared-memory tile buffers per CTA of the TMA kernel:
+    QS_OPT_TMA_BUFFERS = 5,   /* shared-memory tile buffers per CTA of the TMA kernel:
                                  2 (default) or 3                                    */
+    QS_OPT_ADJOINT = 6        /* complex64 adjoint reverse pass: bit 0 set = register-
+                                 staged kernel, clear = TMA kernel (default); bit 1 set
+                                 = two tile buffers in the TMA kernel (default one)  */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open

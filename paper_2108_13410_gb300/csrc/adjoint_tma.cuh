@@ -47,7 +47,7 @@ __device__ __forceinline__ void adj_rotate_w(u64 (&p)[NR], u64 (&l)[NR], unsigne
 }
 
 template <int NBUF>
-__global__ void __launch_bounds__(NT, 1) k_adj_tma(float2 *__restrict__ psi, float2 *__restrict__ lam,
+__global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__restrict__ psi, float2 *__restrict__ lam,
                                                    const double *__restrict__ recs, int rec_stride, int tiles_shift,
                                                    int *__restrict__ err_flag, double *__restrict__ partials,
                                                    int nblk, int slot0, int zinv,
@@ -157,17 +157,21 @@ __global__ void __launch_bounds__(NT, 1) k_adj_tma(float2 *__restrict__ psi, flo
                 for (int i = t; i < nlut; i += NT) lut[i] = make_float2((float)rec[4 + 2 * i], -(float)rec[5 + 2 * i]);
             cur_batch = batch;
         }
+        if (NBUF == 1) {
+            __syncthreads();                 // the single buffer is free again
+            if (t == 0) issue(it);
+        }
         if (t == 0) {
             if (!mbar_wait_bounded(&bars[b], parity, max_wait)) {
                 atomicOr(err_flag, 1);
                 s_ok = 0;
-                for (int j = it; j < it + NBUF - 1 && j < n_my; ++j)
+                for (int j = it; j < it + (NBUF > 1 ? NBUF - 1 : 1) && j < n_my; ++j)
                     mbar_wait_bounded(&bars[j % NBUF], (uint32_t)((j / NBUF) & 1), max_wait);
             }
         }
         __syncthreads();
         if (!s_ok) return;
-        if (t == 0 && it + NBUF - 1 < n_my) issue(it + NBUF - 1);
+        if (NBUF > 1 && t == 0 && it + NBUF - 1 < n_my) issue(it + NBUF - 1);
 
         u64 *tp = reinterpret_cast<u64 *>(buf + (size_t)(2 * b) * (1 << LT));
         u64 *tl = reinterpret_cast<u64 *>(buf + (size_t)(2 * b + 1) * (1 << LT));

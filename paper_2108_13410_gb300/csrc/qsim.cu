@@ -84,6 +84,8 @@ struct qs_sim {
     // persistent TMA X pass (complex64)
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
     int nbuf = 2;                          // TMA shared-memory buffers per CTA (2 or 3)
+    int adj_nbuf = 1;                      // tile buffers of the TMA adjoint pass (1 or 2)
+    int adj_impl = 0;                      // adjoint reverse pass: 0 auto (TMA), 1 register kernel
     int sm_count = 0;
     std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
     std::vector<CUtensorMap> tmaps;        // one per pass, encoded for the bound state
@@ -837,12 +839,13 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
     }
     // ---- reverse sweep ----
     const size_t nblk = (size_t)np * G;
-    const bool use_tma = sizeof(R) == 4 && s->tmaps_ok && s->tmaps_aux_ok && s->xpass_impl != 1;
-    const size_t adj_smem = 2 * 2 * (size_t)TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8;
+    const bool use_tma = sizeof(R) == 4 && s->tmaps_ok && s->tmaps_aux_ok && s->adj_impl != 1;
+    const size_t adj_smem = 2 * (size_t)TMA_TILE_BYTES * s->adj_nbuf + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8;
     unsigned Gt = 1;
     if (use_tma) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_tma<2>, NT, adj_smem);
+        if (s->adj_nbuf == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_tma<1>, NT, adj_smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_tma<2>, NT, adj_smem);
         if (per_sm < 1) per_sm = 1;
         Gt = (unsigned)std::min<long long>((long long)B << (s->n - LT), (long long)per_sm * s->sm_count);
     }
@@ -868,10 +871,16 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
                 TmaPass P = s->tpasses[NVAR * p + V_ROT];
                 P.frame = 1 | ((jj + 1 == nops && pi == 0) ? 2 : 0) | ((jj == 0 && pi == np - 1) ? 4 : 0);
                 const int zinv = (pi == 0 && ops[jj * B].has_z) ? 1 : 0;
-                k_adj_tma<2><<<Gt, NT, adj_smem, s->stream>>>((float2 *)s->state[0], (float2 *)s->state[1], rec,
-                                                            s->rec_stride, s->n - LT, s->d_err, s->d_adj_part,
-                                                            (int)nblk_t, pi * (int)Gt, zinv, s->tmaps[p],
-                                                            s->tmaps_aux[p], P);
+                if (s->adj_nbuf == 1)
+                    k_adj_tma<1><<<Gt, NT, adj_smem, s->stream>>>((float2 *)s->state[0], (float2 *)s->state[1], rec,
+                                                                s->rec_stride, s->n - LT, s->d_err, s->d_adj_part,
+                                                                (int)nblk_t, pi * (int)Gt, zinv, s->tmaps[p],
+                                                                s->tmaps_aux[p], P);
+                else
+                    k_adj_tma<2><<<Gt, NT, adj_smem, s->stream>>>((float2 *)s->state[0], (float2 *)s->state[1], rec,
+                                                                s->rec_stride, s->n - LT, s->d_err, s->d_adj_part,
+                                                                (int)nblk_t, pi * (int)Gt, zinv, s->tmaps[p],
+                                                                s->tmaps_aux[p], P);
                 CKL(s); s->launches++;
             }
             k_finish<<<B, RED_THREADS, 0, s->stream>>>(s->d_adj_part, (int)nblk_t, 4, s->d_grad + jj * B * RED_NV);
@@ -1020,6 +1029,8 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
         cudaFuncSetAttribute(k_xmeasure<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1 << LT) * 16));
         cudaFuncSetAttribute(k_adj_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(4 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
+        cudaFuncSetAttribute(k_adj_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
     }
     size_t smem64 = (size_t)(1 << LT) * 16 + (size_t)s->max_lut * 16;
     cudaFuncSetAttribute(k_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
@@ -1096,6 +1107,11 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
         case QS_OPT_XPASS:
             if (value < 0 || value > 2) FAIL(s, QS_ERR_ARG, "xpass kernel must be 0 (auto), 1 or 2");
             s->xpass_impl = (int)value; return QS_OK;
+        case QS_OPT_ADJOINT:
+            if (value < 0 || value > 3) FAIL(s, QS_ERR_ARG, "adjoint option must be 0..3");
+            s->adj_impl = (value & 1) ? 1 : 0;
+            s->adj_nbuf = (value & 2) ? 2 : 1;
+            return QS_OK;
         case QS_OPT_TMA_BUFFERS:
             if (value != 2 && value != 3) FAIL(s, QS_ERR_ARG, "TMA buffers must be 2 or 3");
             s->nbuf = (int)value; return QS_OK;
