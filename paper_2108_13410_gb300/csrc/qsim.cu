@@ -103,6 +103,8 @@ struct qs_sim {
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_key[10] = {0};
     long long graph_launches = 0;
+    cudaGraphExec_t scan_graph = nullptr;
+    long long scan_key[10] = {0};
     // operator-record inputs (couplings, schedule) on the device
     double *d_in = nullptr; size_t d_in_cap = 0;
     bool in_path = false; size_t in_ncpl = 0;
@@ -354,58 +356,47 @@ void unit_pair(bool f32, double t, double *ou, double *os) {
 }
 
 // ops[k * batch + b].  path: step k uses H1 with couplings c[k * batch + b] (s = 1);
-// otherwise H(s_k) with couplings c[b].
-std::vector<Op> build_ops(const qs_couplings *c0, int batch, const double *sv0, double dt,
+// otherwise H(s_k) with couplings c[b].  Only has_z and the angles of the per-gate form
+// are used on the host; the fused path builds its records on the device.
+std::vector<Op> build_ops(const qs_couplings *c, int batch, const double *sv, double dt,
                           int n_steps, int order, bool fsal, bool path = false) {
     std::vector<Op> ops;
-    std::vector<double> ones;
-    if (path) ones.assign(n_steps, 1.0);
-    const double *sv = path ? ones.data() : sv0;
-    int kcur = 0;   // step whose couplings `c` points at (path mode)
-    auto cpl = [&](int b) -> const qs_couplings & { return path ? c0[(size_t)kcur * batch + b] : c0[b]; };
-    auto xang = [&](int b, double sk, double tau, double *out) {
-        Coef q = coefficients(cpl(b), sk);
-        out[0] = q.xs * tau; out[1] = q.xt * tau;
+    auto cpl = [&](int k, int b) -> const qs_couplings & { return path ? c[(size_t)k * batch + b] : c[b]; };
+    auto sk = [&](int k) -> double { return path ? 1.0 : sv[k]; };
+    auto xang = [&](int k, int b, double tau, double *out) {
+        Coef q = coefficients(cpl(k, b), sk(k));
+        out[0] += q.xs * tau; out[1] += q.xt * tau;
     };
-    struct CView {
-        decltype(cpl) &f;
-        const qs_couplings &operator[](int b) const { return f(b); }
-    } c{cpl};
+    auto zang = [&](int k, int b, Op &o) {
+        Coef q = coefficients(cpl(k, b), sk(k));
+        o.zA = q.za * dt; o.zB = q.zb * dt; o.has_z = true;
+    };
     for (int k = 0; k < n_steps; ++k) {
-        kcur = k;
         if (order == 1) {
             for (int b = 0; b < batch; ++b) {
-                Op o{}; xang(b, sv[k], dt, o.thx);
-                Coef q = coefficients(c[b], sv[k]);
-                o.zA = q.za * dt; o.zB = q.zb * dt; o.has_z = true;
+                Op o{}; xang(k, b, dt, o.thx); zang(k, b, o);
                 ops.push_back(o);
             }
         } else if (fsal) {
             for (int b = 0; b < batch; ++b) {
                 Op o{};
-                double a[2], p[2] = {0.0, 0.0};
-                kcur = k;
-                xang(b, sv[k], 0.5 * dt, a);
-                if (k > 0) { kcur = k - 1; xang(b, sv[k - 1], 0.5 * dt, p); kcur = k; }
-                o.thx[0] = a[0] + p[0]; o.thx[1] = a[1] + p[1];
-                Coef q = coefficients(c[b], sv[k]);
-                o.zA = q.za * dt; o.zB = q.zb * dt; o.has_z = true;
+                xang(k, b, 0.5 * dt, o.thx);
+                if (k > 0) xang(k - 1, b, 0.5 * dt, o.thx);
+                zang(k, b, o);
                 ops.push_back(o);
             }
             if (k == n_steps - 1)
                 for (int b = 0; b < batch; ++b) {
-                    Op o{}; xang(b, sv[k], 0.5 * dt, o.thx); o.has_z = false;
+                    Op o{}; xang(k, b, 0.5 * dt, o.thx);
                     ops.push_back(o);
                 }
         } else {
             for (int b = 0; b < batch; ++b) {
-                Op o{}; xang(b, sv[k], 0.5 * dt, o.thx);
-                Coef q = coefficients(c[b], sv[k]);
-                o.zA = q.za * dt; o.zB = q.zb * dt; o.has_z = true;
+                Op o{}; xang(k, b, 0.5 * dt, o.thx); zang(k, b, o);
                 ops.push_back(o);
             }
             for (int b = 0; b < batch; ++b) {
-                Op o{}; xang(b, sv[k], 0.5 * dt, o.thx); o.has_z = false;
+                Op o{}; xang(k, b, 0.5 * dt, o.thx);
                 ops.push_back(o);
             }
         }
@@ -1055,6 +1046,7 @@ void qs_destroy(qs_sim *s) {
     cudaFree(s->d_scan);
     cudaFree(s->d_in);
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->scan_graph) cudaGraphExecDestroy(s->scan_graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     if (s->h_scan) cudaFreeHost(s->h_scan);
     if (s->h_grad) cudaFreeHost(s->h_grad);
@@ -1394,7 +1386,6 @@ qs_status qs_scan(qs_sim *s, const qs_couplings *points, int n_points, const dou
         }
         if (s->lat.wilson.size() == 2) { P.wx = (uint32_t)s->lat.wilson[0]; P.wy = (uint32_t)s->lat.wilson[1]; }
         P.n_link = s->lat.n_links; P.n_vertex = s->n - s->lat.n_links;
-        CK(s, cudaMemcpyAsync(s->d_scan, s->h_scan, in_doubles * sizeof(double), cudaMemcpyHostToDevice, s->stream));
         int per_sm = 0;
         if (s->dtype == QS_C64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan12<float>, NT, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan12<double>, NT, 0);
@@ -1402,13 +1393,47 @@ qs_status qs_scan(qs_sim *s, const qs_couplings *points, int n_points, const dou
         unsigned grid = (unsigned)std::min<long long>(n_points, (long long)per_sm * s->sm_count);
         const DevCouplings *dc = reinterpret_cast<const DevCouplings *>(s->d_scan);
         double *dout = s->d_scan + in_doubles;
-        if (s->dtype == QS_C64)
-            k_scan12<float><<<grid, NT, 0, s->stream>>>(dc, s->d_scan + 4 * n_points, dout, P);
-        else
-            k_scan12<double><<<grid, NT, 0, s->stream>>>(dc, s->d_scan + 4 * n_points, dout, P);
-        CKL(s); s->launches++;
-        CK(s, cudaMemcpyAsync(s->h_scan + in_doubles, dout, out_doubles * sizeof(double), cudaMemcpyDeviceToHost,
-                              s->stream));
+        // copy-in, the persistent launch and copy-out; with QS_OPT_GRAPH they are captured
+        // once per shape as a CUDA graph and replayed (the copies read and write the
+        // pinned staging buffer at replay time)
+        auto enqueue = [&](cudaStream_t st) -> cudaError_t {
+            cudaError_t e = cudaMemcpyAsync(s->d_scan, s->h_scan, in_doubles * sizeof(double),
+                                            cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return e;
+            if (s->dtype == QS_C64)
+                k_scan12<float><<<grid, NT, 0, st>>>(dc, s->d_scan + 4 * n_points, dout, P);
+            else
+                k_scan12<double><<<grid, NT, 0, st>>>(dc, s->d_scan + 4 * n_points, dout, P);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            return cudaMemcpyAsync(s->h_scan + in_doubles, dout, out_doubles * sizeof(double),
+                                   cudaMemcpyDeviceToHost, st);
+        };
+        if (s->use_graph) {
+            const long long key[10] = {-1, n_points, n_steps, order, (long long)(uintptr_t)s->d_scan,
+                                       (long long)(uintptr_t)s->h_scan, s->dtype, (long long)grid,
+                                       (long long)llround(dt * 1e15), 0};
+            if (!s->scan_graph || memcmp(key, s->scan_key, sizeof(key)) != 0) {
+                if (s->scan_graph) { cudaGraphExecDestroy(s->scan_graph); s->scan_graph = nullptr; }
+                if (!s->cap_stream) CK(s, cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+                CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+                cudaError_t e1 = enqueue(s->cap_stream);
+                cudaGraph_t g = nullptr;
+                cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
+                if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                    if (g) cudaGraphDestroy(g);
+                    FAIL(s, QS_ERR_CUDA, "scan graph capture: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+                }
+                cudaError_t e3 = cudaGraphInstantiate(&s->scan_graph, g, 0);
+                cudaGraphDestroy(g);
+                if (e3 != cudaSuccess) { s->scan_graph = nullptr; FAIL(s, QS_ERR_CUDA, "scan graph: %s", cudaGetErrorString(e3)); }
+                memcpy(s->scan_key, key, sizeof(key));
+            }
+            CK(s, cudaGraphLaunch(s->scan_graph, s->stream));
+        } else {
+            CK(s, enqueue(s->stream));
+        }
+        s->launches++;
         CK(s, cudaStreamSynchronize(s->stream));
         memcpy(out, s->h_scan + in_doubles, out_doubles * sizeof(double));
         return QS_OK;

@@ -79,3 +79,21 @@ def test_scan_point_equals_single_run():
         sim.evolve([cp], s, T / n, 2)
         assert abs(sim.energy([cp])[0] - out[k, 0]) <= 1e-9
         assert abs(sim.expect(QS_PLAQUETTE, -1)[0] - out[k, 1]) <= 1e-9
+
+
+@gpu
+def test_scan_in_a_captured_graph_is_bit_identical():
+    from paper_2108_13410_gb300 import Simulator, QS_OPT_GRAPH
+    pts = [tuple(p) for p in synth.coupling_grid(4, 0.0, 1.5)]
+    T, n = 2.0, 20
+    s = O.schedule_linear(T, n)
+    a = Simulator(2, 2, form="gh", dtype="c64")
+    b = Simulator(2, 2, form="gh", dtype="c64")
+    b.set_option(QS_OPT_GRAPH, 1)
+    ra = a.scan(pts, s, T / n, 2)
+    rb = b.scan(pts, s, T / n, 2)
+    assert np.array_equal(ra, rb)
+    # replay with other couplings and schedule values of the same shape
+    pts2 = [(g + 0.05, l) for g, l in pts]
+    s2 = O.schedule_linear(2 * T, n)
+    assert np.array_equal(a.scan(pts2, s2, T / n, 2), b.scan(pts2, s2, T / n, 2))
