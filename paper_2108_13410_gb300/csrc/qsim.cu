@@ -85,6 +85,7 @@ struct qs_sim {
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
     int nbuf = 2;                          // TMA shared-memory buffers per CTA (2 or 3)
     int adj_nbuf = 1;                      // tile buffers of the TMA adjoint pass (1 or 2)
+    int tma_store = 0;                     // X pass writes tiles back with TMA stores
     int adj_impl = 0;                      // adjoint reverse pass: 0 auto (TMA), 1 register kernel
     int sm_count = 0;
     std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
@@ -428,6 +429,7 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
     if (tma) {
         TmaPass P = s->tpasses[NVAR * p + variant];
         P.frame = frame;
+        P.store_tma = s->tma_store;
         size_t sm = tma_smem_bytes(s, s->nbuf, apply_z);
         int per_sm = 0;
         if (s->nbuf == 3)
@@ -1099,6 +1101,8 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
         case QS_OPT_XPASS:
             if (value < 0 || value > 2) FAIL(s, QS_ERR_ARG, "xpass kernel must be 0 (auto), 1 or 2");
             s->xpass_impl = (int)value; return QS_OK;
+        case QS_OPT_TMA_STORE:
+            s->tma_store = value != 0; return QS_OK;
         case QS_OPT_ADJOINT:
             if (value < 0 || value > 3) FAIL(s, QS_ERR_ARG, "adjoint option must be 0..3");
             s->adj_impl = (value & 1) ? 1 : 0;

@@ -47,6 +47,7 @@ struct TmaPass {
     float scale;                // factor applied with the phase (a power of two)
     int frame;                  // bit 0: rotations in the frame phi_i = i^popc(i) psi_i;
                                 // bit 1: convert psi -> phi at stage A; bit 2: phi -> psi at stage C
+    int store_tma;              // 1: write the tile back with a TMA bulk tensor store
     uint32_t paA_thr[8], pbA_thr[8];  // parity columns of the stage-A thread bits (local 0..7)
     uint32_t paA_reg[NR], pbA_reg[NR];// parity of stage-A register r (local bits 8..11)
 };
@@ -96,6 +97,19 @@ __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, u
 }
 
 __device__ __forceinline__ int swz128(int l) { return l ^ (((l >> 4) & 7) << 1); }
+
+// TMA bulk tensor store of a shared-memory tile (same map and box as the load)
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap *map, const void *src, int c0, int c1, int c2,
+                                             int c3, int c4) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4, %5, %6}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(smem_addr(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // packed FP32x2 fused multiply-add: (a.x * b.x + c.x, a.y * b.y + c.y)
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
@@ -278,6 +292,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         int b = (int)(it % NBUF);
         int x1, x2, x4;
         coords_of(tile, x1, x2, x4);
+        if (P.store_tma) bulk_wait_read_all();   // a store may still be reading this buffer
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&bars[b], TMA_TILE_BYTES);
         tma_load_5d(buf + (size_t)b * (1 << LT), &tmap, &bars[b], 0, x1, x2, 0, x4);
@@ -340,6 +355,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                 // wait (bounded) for every load this CTA still has in flight before leaving
                 for (int j = it; j < it + NBUF - 1 && j < n_my; ++j)
                     mbar_wait_bounded(&bars[j % NBUF], (uint32_t)((j / NBUF) & 1), max_wait);
+                if (P.store_tma) bulk_wait_all();
             }
         }
         __syncthreads();
@@ -414,10 +430,25 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
 #pragma unroll
             for (int r = 0; r < NR; ++r) w[r] = pk(v[r].x, v[r].y);
         }
-        u64 *dst = reinterpret_cast<u64 *>(psi + gbase + toff);
+        if (P.store_tma) {
+            // back into the swizzled tile, then one bulk tensor store of the whole tile
 #pragma unroll
-        for (int r = 0; r < NR; ++r) dst[P.roff_c[r]] = w[r];
+            for (int r = 0; r < NR; ++r) tb[c_base[r & 7] + (r << 4)] = w[r];
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (t == 0) {
+                const int x2 = (int)(tile & ((1ll << P.mid_bits) - 1));
+                const int x4 = (int)(tile >> P.mid_bits);
+                tma_store_5d(&tmap, tb, 0, 0, x2, 0, x4);
+                bulk_commit();
+            }
+        } else {
+            u64 *dst = reinterpret_cast<u64 *>(psi + gbase + toff);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) dst[P.roff_c[r]] = w[r];
+        }
     }
+    if (P.store_tma && t == 0) bulk_wait_all();   // the CTA's shared memory must outlive its stores
 }
 
 }  // namespace qsim

@@ -22,7 +22,8 @@ QS_PERIODIC, QS_OPEN = 0, 1
 QS_GAUGE_HIGGS, QS_UNITARY_GAUGE = 0, 1
 QS_C64, QS_C128 = 0, 1
 QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
-QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_ADJOINT = range(7)
+QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_ADJOINT, \
+    QS_OPT_TMA_STORE = range(8)
 
 
 class QsError(RuntimeError):

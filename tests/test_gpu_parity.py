@@ -249,11 +249,29 @@ def test_errors_are_reported():
 
 
 @gpu
-@pytest.mark.parametrize("impl,nbuf", [(1, 2), (2, 2), (2, 3)])
-def test_complex64_xpass_kernels_agree(impl, nbuf):
+@pytest.mark.parametrize("impl,nbuf,store", [(1, 2, 0), (2, 2, 0), (2, 3, 0), (2, 2, 1), (2, 3, 1)])
+@pytest.mark.parametrize("form", ["ug", "gh"])
+def test_complex64_xpass_kernels_agree(impl, nbuf, store, form):
     """The register-staged and the persistent TMA X-pass kernels (2 or 3 tile
-    buffers) give the oracle's amplitudes on a 20-qubit lattice with batch 2."""
+    buffers, per-thread or bulk tensor stores) give the oracle's amplitudes on a
+    20-qubit unitary-gauge and an 18-qubit gauge-Higgs lattice with batch 2."""
     from paper_2108_13410_gb300 import QS_OPT_XPASS, QS_OPT_TMA_BUFFERS
+    from paper_2108_13410_gb300.qsim import QS_OPT_TMA_STORE
+    if form == "gh":
+        lat = OracleLattice(3, 2, True, "gh")
+        couplings = [(0.6, 0.6), (1.1, 0.3)]
+        s = O.schedule_linear(2.0, 12)
+        sim = _sim(3, 2, form="gh", dtype="c64", batch=2)
+        sim.set_option(QS_OPT_XPASS, impl)
+        sim.set_option(QS_OPT_TMA_BUFFERS, nbuf)
+        sim.set_option(QS_OPT_TMA_STORE, store)
+        sim.init_plus()
+        sim.evolve(couplings, s, 2.0 / 12, 2)
+        sim.sync()
+        got = sim.download().numpy()
+        for b, (g, lam) in enumerate(couplings):
+            _assert_amplitudes(got[b], O.evolve(lat, Couplings(g, lam), s, 2.0 / 12, 2), "c64")
+        return
     lat = OracleLattice(2, 5, True, "ug")          # 20 link qubits, 256 tiles per state
     couplings = [(0.6, 0.6), (1.1, 0.3)]
     T, n = 2.0, 12
@@ -261,6 +279,7 @@ def test_complex64_xpass_kernels_agree(impl, nbuf):
     sim = _sim(2, 5, form="ug", dtype="c64", batch=2)
     sim.set_option(QS_OPT_XPASS, impl)
     sim.set_option(QS_OPT_TMA_BUFFERS, nbuf)
+    sim.set_option(QS_OPT_TMA_STORE, store)
     sim.init_plus()
     sim.evolve(couplings, s, T / n, 2)
     sim.sync()
