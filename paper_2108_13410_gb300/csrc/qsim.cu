@@ -85,7 +85,7 @@ struct qs_sim {
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
     int nbuf = 2;                          // TMA shared-memory buffers per CTA (2 or 3)
     int adj_nbuf = 1;                      // tile buffers of the TMA adjoint pass (1 or 2)
-    int tma_store = 0;                     // X pass writes tiles back with TMA stores
+    int tma_store = 1;                     // X pass writes tiles back with TMA stores
     int adj_impl = 0;                      // adjoint reverse pass: 0 auto (TMA), 1 register kernel
     int sm_count = 0;
     std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
@@ -429,21 +429,15 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
     if (tma) {
         TmaPass P = s->tpasses[NVAR * p + variant];
         P.frame = frame;
-        P.store_tma = s->tma_store;
         size_t sm = tma_smem_bytes(s, s->nbuf, apply_z);
+        auto kern = s->nbuf == 3 ? (s->tma_store ? k_xpass_tma<3, true> : k_xpass_tma<3, false>)
+                                 : (s->tma_store ? k_xpass_tma<2, true> : k_xpass_tma<2, false>);
         int per_sm = 0;
-        if (s->nbuf == 3)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_tma<3>, NT, sm);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_xpass_tma<2>, NT, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm);
         if (per_sm < 1) per_sm = 1;
         long long g = std::min<long long>(P.total_tiles, (long long)per_sm * s->sm_count);
-        if (s->nbuf == 3)
-            k_xpass_tma<3><<<(unsigned)g, NT, sm, s->stream>>>((float2 *)s->state[0], rec, s->rec_stride,
-                                                               s->n - LT, s->d_err, s->tmaps[p], P);
-        else
-            k_xpass_tma<2><<<(unsigned)g, NT, sm, s->stream>>>((float2 *)s->state[0], rec, s->rec_stride,
-                                                               s->n - LT, s->d_err, s->tmaps[p], P);
+        kern<<<(unsigned)g, NT, sm, s->stream>>>((float2 *)s->state[0], rec, s->rec_stride, s->n - LT, s->d_err,
+                                               s->tmaps[p], P);
     } else {
         k_xpass<R><<<grid, NT, smem, s->stream>>>((V<R> *)s->state[0], s->dim, rec, s->rec_stride,
                                                    s->d_passes + NVAR * p + variant);
@@ -1010,9 +1004,13 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
         if (s->sm_count < 1) s->sm_count = 1;
-        cudaFuncSetAttribute(k_xpass_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_xpass_tma<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tma_smem_bytes(s, 2, true));
-        cudaFuncSetAttribute(k_xpass_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_xpass_tma<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(s, 3, true));
+        cudaFuncSetAttribute(k_xpass_tma<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(s, 2, true));
+        cudaFuncSetAttribute(k_xpass_tma<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tma_smem_bytes(s, 3, true));
         int adj64 = (int)(2 * (1 << LT) * 16 + (size_t)(s->nA + 1) * (s->nB + 1) * 16);
         cudaFuncSetAttribute(k_adj_xpass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);

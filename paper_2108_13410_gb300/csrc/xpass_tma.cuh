@@ -47,7 +47,6 @@ struct TmaPass {
     float scale;                // factor applied with the phase (a power of two)
     int frame;                  // bit 0: rotations in the frame phi_i = i^popc(i) psi_i;
                                 // bit 1: convert psi -> phi at stage A; bit 2: phi -> psi at stage C
-    int store_tma;              // 1: write the tile back with a TMA bulk tensor store
     uint32_t paA_thr[8], pbA_thr[8];  // parity columns of the stage-A thread bits (local 0..7)
     uint32_t paA_reg[NR], pbA_reg[NR];// parity of stage-A register r (local bits 8..11)
 };
@@ -240,7 +239,7 @@ __device__ __forceinline__ float2 mul_ipow(float2 v, int k) {
     return r;
 }
 
-template <int NBUF>
+template <int NBUF, bool STORE_TMA>
 __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__restrict__ psi, const double *__restrict__ recs,
                                                   int rec_stride, int tiles_shift,
                                                   int *__restrict__ err_flag,
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         int b = (int)(it % NBUF);
         int x1, x2, x4;
         coords_of(tile, x1, x2, x4);
-        if (P.store_tma) bulk_wait_read_all();   // a store may still be reading this buffer
+        if (STORE_TMA) bulk_wait_read_all();   // a store may still be reading this buffer
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&bars[b], TMA_TILE_BYTES);
         tma_load_5d(buf + (size_t)b * (1 << LT), &tmap, &bars[b], 0, x1, x2, 0, x4);
@@ -355,7 +354,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                 // wait (bounded) for every load this CTA still has in flight before leaving
                 for (int j = it; j < it + NBUF - 1 && j < n_my; ++j)
                     mbar_wait_bounded(&bars[j % NBUF], (uint32_t)((j / NBUF) & 1), max_wait);
-                if (P.store_tma) bulk_wait_all();
+                if (STORE_TMA) bulk_wait_all();
             }
         }
         __syncthreads();
@@ -430,7 +429,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
 #pragma unroll
             for (int r = 0; r < NR; ++r) w[r] = pk(v[r].x, v[r].y);
         }
-        if (P.store_tma) {
+        if (STORE_TMA) {
             // back into the swizzled tile, then one bulk tensor store of the whole tile
 #pragma unroll
             for (int r = 0; r < NR; ++r) tb[c_base[r & 7] + (r << 4)] = w[r];
@@ -448,7 +447,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             for (int r = 0; r < NR; ++r) dst[P.roff_c[r]] = w[r];
         }
     }
-    if (P.store_tma && t == 0) bulk_wait_all();   // the CTA's shared memory must outlive its stores
+    if (STORE_TMA && t == 0) bulk_wait_all();   // the CTA's shared memory must outlive its stores
 }
 
 }  // namespace qsim
