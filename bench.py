@@ -279,7 +279,7 @@ def run_ours(args):
     peak, peak_kind = peaks()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profile_traffic("k_xpass_tma_c64_27q"),
-                "kernel": "k_xpass_tma<2, true>", "launches": xpass_n, "avg_launch_ms": avg_ms,
+                "kernel": "k_xpass_tma<2, false>", "launches": xpass_n, "avg_launch_ms": avg_ms,
                 "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
                 "step_hbm_gbs": (xpass_n / K) * alg_bytes / (ms / K / 1000.0) / 1e9}
 

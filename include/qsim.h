@@ -93,8 +93,8 @@ typedef enum {
     QS_OPT_ADJOINT = 6,       /* complex64 adjoint reverse pass: bit 0 set = register-
                                  staged kernel, clear = TMA kernel (default); bit 1 set
                                  = two tile buffers in the TMA kernel (default one)  */
-    QS_OPT_TMA_STORE = 7      /* 1 (default): the TMA X pass writes each tile back with
-                                 one bulk tensor store; 0: per-thread stores         */
+    QS_OPT_TMA_STORE = 7      /* 1: the TMA X pass writes each tile back with one bulk
+                                 tensor store; 0 (default): per-thread stores        */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open

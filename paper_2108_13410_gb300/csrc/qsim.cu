@@ -85,7 +85,7 @@ struct qs_sim {
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
     int nbuf = 2;                          // TMA shared-memory buffers per CTA (2 or 3)
     int adj_nbuf = 1;                      // tile buffers of the TMA adjoint pass (1 or 2)
-    int tma_store = 1;                     // X pass writes tiles back with TMA stores
+    int tma_store = 0;                     // X pass writes tiles back with TMA stores
     int adj_impl = 0;                      // adjoint reverse pass: 0 auto (TMA), 1 register kernel
     int sm_count = 0;
     std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
