@@ -93,8 +93,14 @@ typedef enum {
     QS_OPT_ADJOINT = 6,       /* complex64 adjoint reverse pass: bit 0 set = register-
                                  staged kernel, clear = TMA kernel (default); bit 1 set
                                  = two tile buffers in the TMA kernel (default one)  */
-    QS_OPT_TMA_STORE = 7      /* 1: the TMA X pass writes each tile back with one bulk
+    QS_OPT_TMA_STORE = 7,     /* 1: the TMA X pass writes each tile back with one bulk
                                  tensor store; 0 (default): per-thread stores        */
+    QS_OPT_XMERGE = 8         /* 1 (default): complex64 gauge-Higgs runs on the TMA
+                                 kernel let consecutive Trotter factor groups share
+                                 the pass of one qubit group (X of group k, the Z layer
+                                 of k, X of group k+1 on the same qubits; exact because
+                                 all X-type factors commute), so a step takes one pass
+                                 fewer; 0: every factor group takes all its passes    */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open
@@ -228,6 +234,11 @@ qs_status qs_load(qs_sim *sim, const char *path);
 /* Total milliseconds and launch count of the fused X-pass kernel since the last
  * read, when QS_OPT_PROFILE is on.  Synchronises the stream. */
 qs_status qs_profile_read(qs_sim *sim, double *total_ms, long long *launches);
+/* The same, split by pass kind: total_ms[2] and launches[2] (host arrays of the
+ * caller), index 0 = passes of one factor group, index 1 = shared passes (X of one
+ * factor group, its Z layer, X of the next group; QS_OPT_XMERGE).  Resets like
+ * qs_profile_read; writes nothing on error. */
+qs_status qs_profile_read_kinds(qs_sim *sim, double *total_ms, long long *launches);
 /* Number of kernels this library launched since the last call (all kinds). */
 long long qs_launch_count(qs_sim *sim);
 

@@ -80,12 +80,14 @@ struct qs_sim {
     double *d_partials = nullptr, *d_res = nullptr, *h_res = nullptr;
     // profiling of the fused pass
     std::vector<cudaEvent_t> ev_pool; size_t ev_used = 0;
+    std::vector<int> ev_kind;              // per timed launch: 0 one factor group, 1 shared pass
     long long launches = 0;
     // persistent TMA X pass (complex64)
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
     int nbuf = 2;                          // TMA shared-memory buffers per CTA (2 or 3)
     int adj_nbuf = 1;                      // tile buffers of the TMA adjoint pass (1 or 2)
     int tma_store = 0;                     // X pass writes tiles back with TMA stores
+    int xmerge = 1;                        // share the pass of one qubit group between factor groups
     int adj_impl = 0;                      // adjoint reverse pass: 0 auto (TMA), 1 register kernel
     int sm_count = 0;
     std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
@@ -250,7 +252,17 @@ void build_tma_passes(qs_sim *s) {
                 if ((r >> kk) & 1) { int q = g(4 + kk); off += 1ll << q; a ^= d.colA[q]; b ^= d.colB[q]; }
             P.roff_c[r] = off; P.pa_reg[r] = a; P.pb_reg[r] = b;
         }
-        for (int j = 0; j < 8; ++j) { int q = g(j); P.paA_thr[j] = d.colA[q]; P.pbA_thr[j] = d.colB[q]; }
+        for (int j = 0; j < 8; ++j) {
+            int q = g(j);
+            P.paA_thr[j] = d.colA[q]; P.pbA_thr[j] = d.colB[q];
+            P.toff_a[j] = 1ll << q;
+        }
+        for (int r = 0; r < NR; ++r) {
+            long long off = 0;
+            for (int kk = 0; kk < RB; ++kk)
+                if ((r >> kk) & 1) off += 1ll << g(8 + kk);
+            P.roff_a[r] = off;
+        }
         for (int r = 0; r < NR; ++r) {
             uint32_t a = 0, b = 0;
             for (int kk = 0; kk < RB; ++kk)
@@ -408,8 +420,24 @@ std::vector<Op> build_ops(const qs_couplings *c, int batch, const double *sv, do
 template <typename R>
 using V = typename C2<R>::T;
 
+typedef void (*XpassTmaKernel)(float2 *, const double *, const double *, int, int, int *, const CUtensorMap,
+                               const TmaPass);
+
+// k_xpass_tma instantiation for (buffers, store mode, merged)
+XpassTmaKernel xpass_tma_kernel(int nbuf, bool store_tma, bool merged) {
+    if (nbuf == 3) {
+        if (merged) return store_tma ? k_xpass_tma<3, true, true> : k_xpass_tma<3, false, true>;
+        return store_tma ? k_xpass_tma<3, true, false> : k_xpass_tma<3, false, false>;
+    }
+    if (merged) return store_tma ? k_xpass_tma<2, true, true> : k_xpass_tma<2, false, true>;
+    return store_tma ? k_xpass_tma<2, true, false> : k_xpass_tma<2, false, false>;
+}
+
+// One X pass.  rec2 != nullptr selects the merged TMA pass: X of the pass's qubits from
+// rec, the Z layer of rec, then X of the same qubits from rec2 (the next factor group).
 template <typename R>
-qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int frame = 0) {
+qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int frame = 0,
+                       const double *rec2 = nullptr) {
     const PassDesc &d = s->pvar[NVAR * p + variant];
     const bool apply_z = d.apply_z != 0;
     dim3 grid((unsigned)(1ll << d.nfixed), (unsigned)s->batch);
@@ -423,6 +451,8 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
         }
         e0 = s->ev_pool[s->ev_used]; e1 = s->ev_pool[s->ev_used + 1];
         s->ev_used += 2;
+        s->ev_kind.resize(s->ev_used / 2);
+        s->ev_kind.back() = rec2 ? 1 : 0;
         CK(s, cudaEventRecord(e0, s->stream));
     }
     const bool tma = sizeof(R) == 4 && s->tmaps_ok && s->xpass_impl != 1;
@@ -430,15 +460,15 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
         TmaPass P = s->tpasses[NVAR * p + variant];
         P.frame = frame;
         size_t sm = tma_smem_bytes(s, s->nbuf, apply_z);
-        auto kern = s->nbuf == 3 ? (s->tma_store ? k_xpass_tma<3, true> : k_xpass_tma<3, false>)
-                                 : (s->tma_store ? k_xpass_tma<2, true> : k_xpass_tma<2, false>);
+        XpassTmaKernel kern = xpass_tma_kernel(s->nbuf, s->tma_store != 0, rec2 != nullptr);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm);
         if (per_sm < 1) per_sm = 1;
         long long g = std::min<long long>(P.total_tiles, (long long)per_sm * s->sm_count);
-        kern<<<(unsigned)g, NT, sm, s->stream>>>((float2 *)s->state[0], rec, s->rec_stride, s->n - LT, s->d_err,
-                                               s->tmaps[p], P);
+        kern<<<(unsigned)g, NT, sm, s->stream>>>((float2 *)s->state[0], rec, rec2 ? rec2 : rec, s->rec_stride,
+                                               s->n - LT, s->d_err, s->tmaps[p], P);
     } else {
+        if (rec2) FAIL(s, QS_ERR_STATE, "merged X pass needs the TMA kernel");
         k_xpass<R><<<grid, NT, smem, s->stream>>>((V<R> *)s->state[0], s->dim, rec, s->rec_stride,
                                                    s->d_passes + NVAR * p + variant);
     }
@@ -700,6 +730,65 @@ qs_status build_records(qs_sim *s, size_t op0, size_t n, double dt, int n_steps,
     return QS_OK;
 }
 
+// The merged schedule applies to the complex64 gauge-Higgs form on the TMA kernel with
+// at least two qubit groups (passes).
+template <typename R>
+bool merged_schedule(const qs_sim *s) {
+    return sizeof(R) == 4 && s->method == 0 && s->xmerge && s->lat.gauge_higgs && s->tmaps_ok &&
+           s->xpass_impl != 1 && s->passes.size() >= 2;
+}
+
+// Factor groups [j0, j1) (records resident from op j0) with shared passes: the last
+// pass of factor group k applies its Z layer and then the next group's X factors on
+// the same qubits, and group k+1 skips that pass.  The shared passes alternate between
+// the two cheapest qubit groups ga = np-2 and gb = np-1 (two register stages each;
+// pass 0 rotates twelve qubits in three stages and always runs alone):
+//   dir 0: ga, 0 .. np-3, gb        dir 1: gb, 0 .. np-3, ga
+// With np passes per X layer a Trotter step costs np - 1 passes instead of np.  Only
+// groups with a Z layer end in a shared pass; at the end of the resident records the
+// chain restarts.
+template <typename R>
+qs_status launch_ops_merged(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit, size_t j0,
+                            size_t j1) {
+    qs_status st;
+    const int B = s->batch;
+    const size_t nops = ops.size() / B;
+    const int np = (int)s->passes.size();
+    const size_t rs = (size_t)B * s->rec_stride;
+    bool carried = false;   // the first qubit group of op k was applied by op k-1's last pass
+    int dir = 0;            // which of the two orders below
+    int ord[2][64];
+    for (int i = 0; i < np; ++i) {
+        const int mid = i - 1;   // middle groups 0 .. np-3
+        ord[0][i] = i == 0 ? np - 2 : (i == np - 1 ? np - 1 : mid);
+        ord[1][i] = i == 0 ? np - 1 : (i == np - 1 ? np - 2 : mid);
+    }
+    for (size_t k = j0; k < j1; ++k) {
+        const double *rec = s->d_rec + (k - j0) * rs;
+        const bool has_z = ops[k * B].has_z;
+        const int i0 = carried ? 1 : 0;
+        carried = false;
+        for (int i = i0; i < np; ++i) {
+            const int p = ord[dir][i];
+            const bool last = i == np - 1;
+            const int frame = 1 | ((k == 0 && i == 0) ? 2 : 0) | ((k + 1 == nops && last) ? 4 : 0);
+            if (last && has_z && k + 1 < j1) {
+                // (the next group may be the trailing X half of a second-order run)
+                if ((st = launch_xpass<R>(s, p, V_ROT_Z, rec, frame, rec + rs)) != QS_OK) return st;
+                carried = true;
+                dir ^= 1;
+            } else {
+                if ((st = launch_xpass<R>(s, p, (last && has_z) ? V_ROT_Z : V_ROT, rec, frame)) != QS_OK)
+                    return st;
+            }
+        }
+        if (s->renorm_every > 0 && steps_per_renorm_unit > 0 &&
+            ((k + 1) % ((size_t)s->renorm_every * steps_per_renorm_unit) == 0 || k + 1 == nops))
+            if ((st = renormalise<R>(s)) != QS_OK) return st;
+    }
+    return QS_OK;
+}
+
 template <typename R>
 qs_status launch_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit, size_t j0 = 0,
                      size_t j1 = (size_t)-1) {
@@ -707,6 +796,7 @@ qs_status launch_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm
     const int B = s->batch;
     const size_t nops = ops.size() / B;
     if (j1 > nops) j1 = nops;
+    if (merged_schedule<R>(s)) return launch_ops_merged<R>(s, ops, steps_per_renorm_unit, j0, j1);
     for (size_t k = j0; k < j1; ++k) {
         if (s->method == 0)
             st = run_op_fused<R>(s, &ops[k * B], s->d_rec + (k - j0) * B * (size_t)s->rec_stride, k, nops);
@@ -743,7 +833,8 @@ qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_un
     // Replay the launch sequence as a CUDA graph, captured once per configuration on a
     // private stream; the records it reads are rebuilt in place before every replay.
     const long long key[10] = {(long long)nops, order, n_steps, B, (long long)(uintptr_t)s->state[0],
-                               (long long)(uintptr_t)s->d_rec, s->renorm_every, s->xpass_impl * 16 + s->nbuf,
+                               (long long)(uintptr_t)s->d_rec, s->renorm_every,
+                               s->xpass_impl * 16 + s->nbuf + 256 * s->tma_store + 1024 * s->xmerge,
                                s->method, (long long)s->dtype};
     if (!s->graph_exec || memcmp(key, s->graph_key, sizeof(key)) != 0) {
         if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
@@ -1004,14 +1095,10 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
         if (s->sm_count < 1) s->sm_count = 1;
-        cudaFuncSetAttribute(k_xpass_tma<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tma_smem_bytes(s, 2, true));
-        cudaFuncSetAttribute(k_xpass_tma<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tma_smem_bytes(s, 3, true));
-        cudaFuncSetAttribute(k_xpass_tma<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tma_smem_bytes(s, 2, true));
-        cudaFuncSetAttribute(k_xpass_tma<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tma_smem_bytes(s, 3, true));
+        for (int nb = 2; nb <= 3; ++nb)
+            for (int v = 0; v < 4; ++v)
+                cudaFuncSetAttribute(xpass_tma_kernel(nb, v & 1, (v >> 1) & 1),
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(s, nb, true));
         int adj64 = (int)(2 * (1 << LT) * 16 + (size_t)(s->nA + 1) * (s->nB + 1) * 16);
         cudaFuncSetAttribute(k_adj_xpass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_adj_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
@@ -1101,6 +1188,8 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
             s->xpass_impl = (int)value; return QS_OK;
         case QS_OPT_TMA_STORE:
             s->tma_store = value != 0; return QS_OK;
+        case QS_OPT_XMERGE:
+            s->xmerge = value != 0; return QS_OK;
         case QS_OPT_ADJOINT:
             if (value < 0 || value > 3) FAIL(s, QS_ERR_ARG, "adjoint option must be 0..3");
             s->adj_impl = (value & 1) ? 1 : 0;
@@ -1636,18 +1725,32 @@ qs_status qs_sync(qs_sim *s) {
     return check_device_flag(s);
 }
 
-qs_status qs_profile_read(qs_sim *s, double *total_ms, long long *count) {
+qs_status qs_profile_read_kinds(qs_sim *s, double *total_ms, long long *count) {
     if (!s || !total_ms || !count) return QS_ERR_ARG;
     CK(s, cudaStreamSynchronize(s->stream));
-    double tot = 0.0;
+    double t[2] = {0.0, 0.0};
+    long long c[2] = {0, 0};
     for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
         float ms = 0.f;
         CK(s, cudaEventElapsedTime(&ms, s->ev_pool[i], s->ev_pool[i + 1]));
-        tot += ms;
+        const int kd = s->ev_kind[i / 2];
+        t[kd] += ms;
+        c[kd] += 1;
     }
-    *total_ms = tot;
-    *count = (long long)(s->ev_used / 2);
+    for (int kd = 0; kd < 2; ++kd) { total_ms[kd] = t[kd]; count[kd] = c[kd]; }
     s->ev_used = 0;
+    s->ev_kind.clear();
+    return QS_OK;
+}
+
+qs_status qs_profile_read(qs_sim *s, double *total_ms, long long *count) {
+    if (!s || !total_ms || !count) return QS_ERR_ARG;
+    double t[2];
+    long long c[2];
+    qs_status st = qs_profile_read_kinds(s, t, c);
+    if (st != QS_OK) return st;
+    *total_ms = t[0] + t[1];
+    *count = c[0] + c[1];
     return QS_OK;
 }
 

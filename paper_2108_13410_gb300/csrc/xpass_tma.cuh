@@ -49,6 +49,8 @@ struct TmaPass {
                                 // bit 1: convert psi -> phi at stage A; bit 2: phi -> psi at stage C
     uint32_t paA_thr[8], pbA_thr[8];  // parity columns of the stage-A thread bits (local 0..7)
     uint32_t paA_reg[NR], pbA_reg[NR];// parity of stage-A register r (local bits 8..11)
+    long long toff_a[8];        // stage A: global offset of thread bit j (local 0..7)
+    long long roff_a[NR];       // stage A: global offset of register r (local bits 8..11)
 };
 
 constexpr int TMA_TILE_BYTES = (1 << LT) * 8;
@@ -239,8 +241,14 @@ __device__ __forceinline__ float2 mul_ipow(float2 v, int k) {
     return r;
 }
 
-template <int NBUF, bool STORE_TMA>
+// MERGED: the pass applies X(G) of one factor group, the Z layer, then X(G) of the
+// next factor group (recs2), for the same tile qubits G.  All X-type factors commute,
+// so consecutive factor groups that take their qubit groups in opposite orders share
+// the pass that holds G (one HBM round trip fewer per Trotter step).  The second round
+// runs stages C, B, A and stores from the stage-A layout.
+template <int NBUF, bool STORE_TMA, bool MERGED>
 __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__restrict__ psi, const double *__restrict__ recs,
+                                                  const double *__restrict__ recs2,
                                                   int rec_stride, int tiles_shift,
                                                   int *__restrict__ err_flag,
                                                   const __grid_constant__ CUtensorMap tmap,
@@ -254,6 +262,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
     uint2 *ptab = reinterpret_cast<uint2 *>(lut + (P.apply_z ? (P.nA + 1) * (P.nB + 1) : 0));  // 3 x 256
     __shared__ uint64_t bars[NBUF];
     __shared__ int s_ok;
+    __shared__ RotConst s_rc2;     // MERGED: rotation constants of the second round
 
     const int t = threadIdx.x;
     const long long G = gridDim.x;
@@ -317,6 +326,12 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         if ((tlo >> j) & 1) { toff += P.toff_c[j]; pa_t ^= P.pa_thr[j]; pb_t ^= P.pb_thr[j]; }
         if ((thi >> j) & 1) { toff += P.toff_c[4 + j]; pa_t ^= P.pa_thr[4 + j]; pb_t ^= P.pb_thr[4 + j]; }
     }
+    long long toff_a = 0;                             // MERGED: stage-A store offset
+    if (MERGED) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if ((t >> j) & 1) toff_a += P.toff_a[j];
+    }
     const int nB1 = P.nB + 1;
     const int nlut = (P.nA + 1) * nB1;
     const bool had = P.hadamard != 0;
@@ -345,6 +360,12 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             if (P.apply_z)
                 for (int i = t; i < nlut; i += NT)
                     lut[i] = make_float2((float)rec[P.lut_off + 2 * i], (float)rec[P.lut_off + 2 * i + 1]);
+            if (MERGED && t == 0) {
+                const double *r2 = recs2 + batch * rec_stride;
+                const float v0 = (float)r2[0], w0 = (float)r2[1], v1 = (float)r2[2], w1 = (float)r2[3];
+                s_rc2.nu[0] = pk(-v0, -v0); s_rc2.ps[0] = pk(w0, w0); s_rc2.ns[0] = pk(-w0, -w0);
+                s_rc2.nu[1] = pk(-v1, -v1); s_rc2.ps[1] = pk(w1, w1); s_rc2.ns[1] = pk(-w1, -w1);
+            }
             cur_batch = batch;
         }
         if (t == 0) {
@@ -421,7 +442,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                     for (int r = 0; r < NR; ++r) { v[r].x *= P.scale; v[r].y *= P.scale; }
                 }
             }
-            if (P.frame & 4) {
+            if (!MERGED && (P.frame & 4)) {
                 const int k0 = -(__popc(tlo) + __popc(thi) + pc_tile);
 #pragma unroll
                 for (int r = 0; r < NR; ++r) v[r] = mul_ipow(v[r], (k0 - __popc(r)) & 3);
@@ -429,7 +450,62 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
 #pragma unroll
             for (int r = 0; r < NR; ++r) w[r] = pk(v[r].x, v[r].y);
         }
-        if (STORE_TMA) {
+        if (MERGED) {
+            // ---- second round: stage C (still in registers), B, A; store from A ----
+            {
+                const RotConst R2 = s_rc2;
+                rotate_w(w, P.rot[2], cls2, R2);
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) tb[c_base[r & 7] + (r << 4)] = w[r];
+            __syncthreads();
+            if (P.stage_b) {
+                ulonglong2 *tb2 = reinterpret_cast<ulonglong2 *>(tb);
+#pragma unroll
+                for (int m = 0; m < NR / 2; ++m) {
+                    const ulonglong2 q = tb2[b_base + (m ^ b_x)];
+                    w[2 * m] = q.x;
+                    w[2 * m + 1] = q.y;
+                }
+                {
+                    const RotConst R2 = s_rc2;
+                    rotate_w(w, P.rot[1], cls1, R2);
+                }
+#pragma unroll
+                for (int m = 0; m < NR / 2; ++m) tb2[b_base + (m ^ b_x)] = make_ulonglong2(w[2 * m], w[2 * m + 1]);
+                __syncthreads();
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) w[r] = tb[a_base + (r << TB)];
+            {
+                const RotConst R2 = s_rc2;
+                rotate_w(w, P.rot[0], cls0, R2);
+            }
+            if (P.frame & 4) {
+                const int k0 = -(__popc(t) + pc_tile);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const float2 v = mul_ipow(unpk(w[r]), (k0 - __popc(r)) & 3);
+                    w[r] = pk(v.x, v.y);
+                }
+            }
+            if (STORE_TMA) {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) tb[a_base + (r << TB)] = w[r];
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncthreads();
+                if (t == 0) {
+                    const int x2 = (int)(tile & ((1ll << P.mid_bits) - 1));
+                    const int x4 = (int)(tile >> P.mid_bits);
+                    tma_store_5d(&tmap, tb, 0, 0, x2, 0, x4);
+                    bulk_commit();
+                }
+            } else {
+                u64 *dst = reinterpret_cast<u64 *>(psi + gbase + toff_a);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) dst[P.roff_a[r]] = w[r];
+            }
+        } else if (STORE_TMA) {
             // back into the swizzled tile, then one bulk tensor store of the whole tile
 #pragma unroll
             for (int r = 0; r < NR; ++r) tb[c_base[r & 7] + (r << 4)] = w[r];

@@ -23,7 +23,7 @@ QS_GAUGE_HIGGS, QS_UNITARY_GAUGE = 0, 1
 QS_C64, QS_C128 = 0, 1
 QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
 QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_ADJOINT, \
-    QS_OPT_TMA_STORE = range(8)
+    QS_OPT_TMA_STORE, QS_OPT_XMERGE = range(9)
 
 
 class QsError(RuntimeError):
@@ -76,6 +76,7 @@ _SIGS = {
     "qs_scan": ([_P, _CP, _I, _DP, _D, _I, _I, _DP], _I),
     "qs_adjoint_grad": ([_P, _CP, _DP, _D, _I, _I, _I, _P, _DP, _DP], _I),
     "qs_profile_read": ([_P, _DP, ctypes.POINTER(_LL)], _I),
+    "qs_profile_read_kinds": ([_P, _DP, ctypes.POINTER(_LL)], _I),
     "qs_launch_count": ([_P], _LL),
     "qs_expect_z_noalloc": ([_P, _I, _I, _I, _U64, _P, _P], _I),
 }
@@ -294,6 +295,14 @@ def qs_profile_read(sim):
     return ms.value, cnt.value
 
 
+def qs_profile_read_kinds(sim):
+    """((ms, launches) of passes of one factor group, (ms, launches) of shared passes)."""
+    ms = (ctypes.c_double * 2)()
+    cnt = (_LL * 2)()
+    _check(sim, library().qs_profile_read_kinds(sim, ms, cnt))
+    return (ms[0], cnt[0]), (ms[1], cnt[1])
+
+
 def qs_launch_count(sim) -> int:
     return library().qs_launch_count(sim)
 
@@ -463,6 +472,9 @@ class Simulator:
 
     def profile_read(self):
         return qs_profile_read(self.h)
+
+    def profile_read_kinds(self):
+        return qs_profile_read_kinds(self.h)
 
     def launch_count(self):
         return qs_launch_count(self.h)

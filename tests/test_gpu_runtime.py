@@ -54,20 +54,49 @@ def test_renormalisation_keeps_unit_norm_and_the_state():
 @gpu
 @pytest.mark.parametrize("dtype", ["c64", "c128"])
 def test_checkpoint_resume_is_bit_identical(tmp_path, dtype):
+    """Save after 9 of 20 first-order steps, load into a new simulator, finish: the
+    state is bit-identical to the same two calls without the checkpoint.  Splitting
+    the run into two calls is itself exact with separate passes (complex128 here);
+    with shared passes (complex64) the first X factors of the second call meet their
+    qubit groups in another order, which changes rounding only."""
+    from paper_2108_13410_gb300.qsim import QS_OPT_XMERGE
     T, n = 2.0, 20
     s = O.schedule_linear(T, n)
+    cpl = [(0.6, 0.6)]
     full = _sim(3, 2, form="gh", dtype=dtype)
     full.init_plus()
-    full.evolve([(0.6, 0.6)], s, T / n, 1)
+    full.evolve(cpl, s, T / n, 1)
+    two = _sim(3, 2, form="gh", dtype=dtype)
+    two.init_plus()
+    two.evolve(cpl, s[:9], T / n, 1)
+    two.evolve(cpl, s[9:], T / n, 1)
     part = _sim(3, 2, form="gh", dtype=dtype)
     part.init_plus()
-    part.evolve([(0.6, 0.6)], s[:9], T / n, 1)
+    part.evolve(cpl, s[:9], T / n, 1)
     path = str(tmp_path / "ckpt.qs")
     part.save(path)
     resumed = _sim(3, 2, form="gh", dtype=dtype)
     resumed.load(path)
-    resumed.evolve([(0.6, 0.6)], s[9:], T / n, 1)
-    assert np.array_equal(full.download().numpy(), resumed.download().numpy())
+    resumed.evolve(cpl, s[9:], T / n, 1)
+    assert np.array_equal(two.download().numpy(), resumed.download().numpy())
+    a = full.download().numpy().astype(np.complex128)
+    b = resumed.download().numpy().astype(np.complex128)
+    if dtype == "c128":
+        assert np.array_equal(a, b)
+    else:
+        assert np.linalg.norm(a - b) <= 1e-6
+        # separate passes: the split is exact in complex64 too
+        for sim in (full, part, resumed):
+            sim.set_option(QS_OPT_XMERGE, 0)
+        full.init_plus()
+        full.evolve(cpl, s, T / n, 1)
+        part.init_plus()
+        part.evolve(cpl, s[:9], T / n, 1)
+        path2 = str(tmp_path / "ckpt2.qs")
+        part.save(path2)
+        resumed.load(path2)
+        resumed.evolve(cpl, s[9:], T / n, 1)
+        assert np.array_equal(full.download().numpy(), resumed.download().numpy())
     other = _sim(2, 2, form="gh", dtype=dtype)
     from paper_2108_13410_gb300 import QsError
     with pytest.raises(QsError):
@@ -95,12 +124,19 @@ def test_bounded_wait_times_out_and_the_context_survives():
 
 @gpu
 def test_launch_count_is_reported():
+    from paper_2108_13410_gb300.qsim import QS_OPT_XMERGE
     sim = _sim(3, 3, form="gh", dtype="c64")
     sim.init_plus()
     sim.launch_count()
     sim.evolve([(0.6, 0.6)], O.schedule_linear(1.0, 10), 0.1, 2)
     sim.sync()
-    # device-built records (1) + 3 passes x 10 steps + 3 trailing passes
+    # device-built records (1) + 3 passes for the first factor group + 2 for each of
+    # the other 10 (9 steps and the trailing X half): they share one pass each
+    assert sim.launch_count() == 1 + 3 + 2 * 10
+    sim.set_option(QS_OPT_XMERGE, 0)
+    sim.evolve([(0.6, 0.6)], O.schedule_linear(1.0, 10), 0.1, 2)
+    sim.sync()
+    # separate passes: 3 x 10 steps + 3 trailing passes
     assert sim.launch_count() == 1 + 3 * 11
 
 
