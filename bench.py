@@ -275,7 +275,7 @@ def run_ours(args):
     state_bytes = sim.state_bytes
     alg_bytes = 2.0 * state_bytes                     # one read + one write of the state per pass
     peak, peak_kind = peaks()
-    names = ("k_xpass_tma<2, false, false>", "k_xpass_tma<2, false, true>")
+    names = ("k_xpass_tma<3, true, false, true>", "k_xpass_tma<3, true, true, true>")
     tags = ("k_xpass_tma_c64_27q", "k_xpass_tma_shared_c64_27q")
     dom = 0 if kinds[0][0] >= kinds[1][0] else 1     # dominant kernel: larger total time
     per_kind = {}

@@ -89,12 +89,12 @@ typedef enum {
     QS_OPT_XPASS = 4,         /* X-pass kernel for complex64: 0 auto (TMA), 1 the
                                  register-staged kernel, 2 the persistent TMA kernel */
     QS_OPT_TMA_BUFFERS = 5,   /* shared-memory tile buffers per CTA of the TMA kernel:
-                                 2 (default) or 3                                    */
+                                 2 (three CTAs per SM) or 3 (default; two CTAs per SM) */
     QS_OPT_ADJOINT = 6,       /* complex64 adjoint reverse pass: bit 0 set = register-
                                  staged kernel, clear = TMA kernel (default); bit 1 set
                                  = two tile buffers in the TMA kernel (default one)  */
-    QS_OPT_TMA_STORE = 7,     /* 1: the TMA X pass writes each tile back with one bulk
-                                 tensor store; 0 (default): per-thread stores        */
+    QS_OPT_TMA_STORE = 7,     /* 1 (default): the TMA X pass writes each tile back with
+                                 one bulk tensor store; 0: per-thread stores         */
     QS_OPT_XMERGE = 8         /* 1 (default): complex64 gauge-Higgs runs on the TMA
                                  kernel let consecutive Trotter factor groups share
                                  the pass of one qubit group (X of group k, the Z layer
@@ -211,11 +211,12 @@ int qs_num_links(const qs_sim *sim);
 qs_status qs_dos(qs_sim *sim, double *out);
 
 /* Autotuner: times n_steps second-order steps of every X-pass configuration that
- * applies (complex64: the persistent TMA kernel with 2 or 3 tile buffers, and the
- * register-staged kernel; complex128: the register-staged kernel) on the bound
- * state, which is overwritten, and keeps the fastest (QS_OPT_XPASS,
- * QS_OPT_TMA_BUFFERS).  Outputs the choice and its ms per step (host). */
-qs_status qs_autotune(qs_sim *sim, int n_steps, int *best_xpass, int *best_buffers,
+ * applies (complex64: the persistent TMA kernel with 2 or 3 tile buffers and either
+ * store mode, and the register-staged kernel; complex128: the register-staged kernel)
+ * on the bound state, which is overwritten, and keeps the fastest (QS_OPT_XPASS,
+ * QS_OPT_TMA_BUFFERS, QS_OPT_TMA_STORE).  Outputs the choice and its ms per step
+ * (host). */
+qs_status qs_autotune(qs_sim *sim, int n_steps, int *best_xpass, int *best_buffers, int *best_store,
                       double *best_ms_per_step);
 
 /* Failure-detection self-test: launches a kernel that waits on an mbarrier which

@@ -53,7 +53,10 @@ struct PassDesc {
 
 // Operator record (doubles): [u_sigma, s_sigma, u_tau, s_tau, then (nA+1)(nB+1)
 //   phase pairs (u, s) of exp(i phi(nA_odd, nB_odd))], where exp(i t) = (1 - u) + i s,
-//   u = 1 - cos t, s = sin t (u keeps full relative precision for small angles).
+//   u = 1 - cos t, s = sin t (u keeps full relative precision for small angles);
+//   then the Hadamard-basis X table (unitary gauge) and, at tan_off, the tangent form
+//   (t_sigma, t_tau, C, 0) of the X layer (dev_tan_triple) followed by the Z table
+//   scaled by C (dev_scaled_pair; same layout as the plain Z table).
 __host__ __device__ inline int record_doubles(int nA, int nB) {
     int r = 4 + 2 * (nA + 1) * (nB + 1);
     return (r + 1) & ~1;
@@ -499,6 +502,7 @@ struct RecGeom {
     int batch, rec_stride;
     int nA, nB, nXA, nXB, xlut_off;
     int f32;
+    int tan_off, nX0, nX1;       // tangent-form triple (0: none); X qubits per class
     double dt;
 };
 
@@ -561,13 +565,58 @@ __device__ inline void dev_op_angles(const RecGeom &G, const DevCouplings *__res
     }
 }
 
+// Tangent form of one X layer for the complex64 kernels.  In the real-rotation frame
+// exp(i th X) is cos th [[1, t], [-t, 1]] with t = tan th: a butterfly a' = a + t b,
+// b' = b - t a (one rounded FMA per output), and the cos th of all n0 + n1 X qubits
+// multiply to one scalar C, applied once per factor group.  t is rounded to the kernel
+// precision and C is computed in FP64 from the rounded t, C = (1 + t0^2)^(-n0/2)
+// (1 + t1^2)^(-n1/2), so the butterflies and C together keep the norm exactly; C is
+// applied through the scaled Z table (dev_scaled_pair) or, for a factor group without
+// a Z layer, rounded once.  Used when |th| <= pi/4 and C >= 1/2 (the host checks;
+// otherwise the (u, s) form runs).  o = [t0, t1, C, 0].
+__device__ inline void dev_tan_triple(bool f32, double th0, double th1, int n0, int n1, double *o) {
+    double t0 = tan(th0), t1 = tan(th1);
+    if (f32) { t0 = (double)(float)t0; t1 = (double)(float)t1; }
+    o[0] = t0; o[1] = t1;
+    o[2] = pow(1.0 + t0 * t0, -0.5 * n0) * pow(1.0 + t1 * t1, -0.5 * n1);
+    o[3] = 0.0;
+}
+
+// C exp(i phi) as (u, s) with (1 - u) + i s, u = 1 - C cos phi, s = C sin phi; for
+// complex64 the float pair within +-3 ulps of each component minimising
+// |(1 - u)^2 + s^2 - C^2| (in double), so the modulus of every table entry is C to
+// ~1e-10 relative, as the unit pairs of dev_unit_pair are 1.
+__device__ inline void dev_scaled_pair(bool f32, double phi, double C, double *ou, double *os) {
+    const double sh = sin(0.5 * phi);
+    const double u = (1.0 - C) + C * 2.0 * sh * sh, s = C * sin(phi);
+    if (!f32) { *ou = u; *os = s; return; }
+    const double C2 = C * C;
+    float u0 = (float)u, s0 = (float)s, bu = u0, bs = s0;
+    double c0 = 1.0 - (double)u0;
+    double be = fabs(c0 * c0 + (double)s0 * (double)s0 - C2), bd = 0.0;
+    float uu = u0;
+    for (int i = 0; i < 3; ++i) uu = nextafterf(uu, -4.0f);
+    for (int i = -3; i <= 3; ++i, uu = nextafterf(uu, 4.0f)) {
+        float ss = s0;
+        for (int j = 0; j < 3; ++j) ss = nextafterf(ss, -4.0f);
+        for (int j = -3; j <= 3; ++j, ss = nextafterf(ss, 4.0f)) {
+            const double c = 1.0 - (double)uu;
+            const double e = fabs(c * c + (double)ss * (double)ss - C2);
+            const double dd = fabs((double)uu - u) + fabs((double)ss - s);
+            if (e < be || (e == be && dd < bd)) { be = e; bd = dd; bu = uu; bs = ss; }
+        }
+    }
+    *ou = bu; *os = bs;
+}
+
 // one thread per (op, batch, entry); entry 0 = X header, then Z table, then X table;
 // records of ops op0 .. op0 + n_ops - 1 are written from recs[0]
 __global__ void k_build_records(RecGeom G, const DevCouplings *__restrict__ cpl, const double *__restrict__ sv,
                                 int op0, int n_ops, double *__restrict__ recs) {
     const int nz = (G.nA + 1) * (G.nB + 1);
     const int nx = G.xlut_off > 0 ? (G.nXA + 1) * (G.nXB + 1) : 0;
-    const long long per = 1 + nz + nx;
+    const int nt = G.tan_off > 0 ? nz : 0;
+    const long long per = 1 + nz + nx + nt;
     const long long total = (long long)n_ops * G.batch * per;
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
          id += (long long)gridDim.x * blockDim.x) {
@@ -581,14 +630,23 @@ __global__ void k_build_records(RecGeom G, const DevCouplings *__restrict__ cpl,
         if (e == 0) {
             dev_unit_pair(G.f32, thx[0], &r[0], &r[1]);
             dev_unit_pair(G.f32, thx[1], &r[2], &r[3]);
+            if (G.tan_off > 0) dev_tan_triple(G.f32, thx[0], thx[1], G.nX0, G.nX1, &r[G.tan_off]);
         } else if (e <= nz) {
             const int k = e - 1, a = k / (G.nB + 1), bb = k % (G.nB + 1);
             double phi = has_z ? zA * (double)(G.nA - 2 * a) + zB * (double)(G.nB - 2 * bb) : 0.0;
             dev_unit_pair(G.f32, phi, &r[4 + 2 * k], &r[5 + 2 * k]);
-        } else {
+        } else if (e <= nz + nx) {
             const int k = e - 1 - nz, a = k / (G.nXB + 1), bb = k % (G.nXB + 1);
             double phi = thx[1] * (double)(G.nXA - 2 * a) + thx[0] * (double)(G.nXB - 2 * bb);
             dev_unit_pair(G.f32, phi, &r[G.xlut_off + 2 * k], &r[G.xlut_off + 2 * k + 1]);
+        } else {
+            // Z table scaled by the tangent form's C
+            const int k = e - 1 - nz - nx, a = k / (G.nB + 1), bb = k % (G.nB + 1);
+            double tc[4];
+            dev_tan_triple(G.f32, thx[0], thx[1], G.nX0, G.nX1, tc);
+            double phi = has_z ? zA * (double)(G.nA - 2 * a) + zB * (double)(G.nB - 2 * bb) : 0.0;
+            double *tl = r + G.tan_off + 4;
+            dev_scaled_pair(G.f32, phi, tc[2], &tl[2 * k], &tl[2 * k + 1]);
         }
     }
 }

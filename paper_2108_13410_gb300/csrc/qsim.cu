@@ -84,10 +84,13 @@ struct qs_sim {
     long long launches = 0;
     // persistent TMA X pass (complex64)
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
-    int nbuf = 2;                          // TMA shared-memory buffers per CTA (2 or 3)
+    int nbuf = 3;                          // TMA shared-memory buffers per CTA (2 or 3)
     int adj_nbuf = 1;                      // tile buffers of the TMA adjoint pass (1 or 2)
-    int tma_store = 0;                     // X pass writes tiles back with TMA stores
+    int tma_store = 1;                     // X pass writes tiles back with TMA stores
     int xmerge = 1;                        // share the pass of one qubit group between factor groups
+    int tan_off = 0;                       // tangent triple in the operator record
+    int nX0 = 0, nX1 = 0;                  // X qubits per class
+    bool tan_active = false;               // this call's X passes use the tangent form
     int adj_impl = 0;                      // adjoint reverse pass: 0 auto (TMA), 1 register kernel
     int sm_count = 0;
     std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
@@ -284,6 +287,7 @@ void build_tma_passes(qs_sim *s) {
         P.lut_off = d.lut_off;
         P.scale = (float)d.scale;
         P.tile_bits = n - LT;
+        P.tan_off = s->tan_off;
         for (int i = 0; i < P.tile_bits && i < 32; ++i) {
             int q = i < P.mid_bits ? P.c + i : P.next + P.k + (i - P.mid_bits);
             P.pa_tile[i] = d.colA[q]; P.pb_tile[i] = d.colB[q];
@@ -423,21 +427,25 @@ using V = typename C2<R>::T;
 typedef void (*XpassTmaKernel)(float2 *, const double *, const double *, int, int, int *, const CUtensorMap,
                                const TmaPass);
 
-// k_xpass_tma instantiation for (buffers, store mode, merged)
-XpassTmaKernel xpass_tma_kernel(int nbuf, bool store_tma, bool merged) {
-    if (nbuf == 3) {
-        if (merged) return store_tma ? k_xpass_tma<3, true, true> : k_xpass_tma<3, false, true>;
-        return store_tma ? k_xpass_tma<3, true, false> : k_xpass_tma<3, false, false>;
-    }
-    if (merged) return store_tma ? k_xpass_tma<2, true, true> : k_xpass_tma<2, false, true>;
-    return store_tma ? k_xpass_tma<2, true, false> : k_xpass_tma<2, false, false>;
+template <int NBUF, bool TAN>
+XpassTmaKernel xpass_tma_kernel_nb(bool store_tma, bool merged) {
+    if (merged) return store_tma ? k_xpass_tma<NBUF, true, true, TAN> : k_xpass_tma<NBUF, false, true, TAN>;
+    return store_tma ? k_xpass_tma<NBUF, true, false, TAN> : k_xpass_tma<NBUF, false, false, TAN>;
+}
+
+// k_xpass_tma instantiation for (buffers, store mode, shared pass, tangent form); shared
+// passes exist in the tangent form only
+XpassTmaKernel xpass_tma_kernel(int nbuf, bool store_tma, bool merged, bool tan) {
+    if (tan) return nbuf == 3 ? xpass_tma_kernel_nb<3, true>(store_tma, merged)
+                              : xpass_tma_kernel_nb<2, true>(store_tma, merged);
+    return nbuf == 3 ? xpass_tma_kernel_nb<3, false>(store_tma, false) : xpass_tma_kernel_nb<2, false>(store_tma, false);
 }
 
 // One X pass.  rec2 != nullptr selects the merged TMA pass: X of the pass's qubits from
 // rec, the Z layer of rec, then X of the same qubits from rec2 (the next factor group).
 template <typename R>
 qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int frame = 0,
-                       const double *rec2 = nullptr) {
+                       const double *rec2 = nullptr, int xscale = 0) {
     const PassDesc &d = s->pvar[NVAR * p + variant];
     const bool apply_z = d.apply_z != 0;
     dim3 grid((unsigned)(1ll << d.nfixed), (unsigned)s->batch);
@@ -459,8 +467,11 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
     if (tma) {
         TmaPass P = s->tpasses[NVAR * p + variant];
         P.frame = frame;
+        const bool tan = s->tan_active && (frame & 1);
+        if (rec2 && !tan) FAIL(s, QS_ERR_STATE, "shared X pass needs the tangent form");
+        P.xscale = tan ? xscale : 0;
         size_t sm = tma_smem_bytes(s, s->nbuf, apply_z);
-        XpassTmaKernel kern = xpass_tma_kernel(s->nbuf, s->tma_store != 0, rec2 != nullptr);
+        XpassTmaKernel kern = xpass_tma_kernel(s->nbuf, s->tma_store != 0, rec2 != nullptr, tan);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm);
         if (per_sm < 1) per_sm = 1;
@@ -521,7 +532,9 @@ qs_status run_op_fused(qs_sim *s, const Op *ops_b, const double *drec, size_t k 
             bool z_here = has_z && p == np - 1;
             int frame = 0;
             if (tma) frame = 1 | ((k == 0 && p == 0) ? 2 : 0) | ((k + 1 == nops && p == np - 1) ? 4 : 0);
-            if ((st = launch_xpass<R>(s, p, z_here ? V_ROT_Z : V_ROT, drec, frame)) != QS_OK) return st;
+            const int xs = (!has_z && p == np - 1) ? 1 : 0;   // tangent form: C of a group without Z
+            if ((st = launch_xpass<R>(s, p, z_here ? V_ROT_Z : V_ROT, drec, frame, nullptr, xs)) != QS_OK)
+                return st;
         }
         return QS_OK;
     } else {
@@ -719,8 +732,11 @@ qs_status build_records(qs_sim *s, size_t op0, size_t n, double dt, int n_steps,
     G.nA = s->nA; G.nB = s->nB; G.nXA = s->nXA; G.nXB = s->nXB;
     G.xlut_off = s->lat.gauge_higgs ? 0 : s->xlut_off;
     G.f32 = s->dtype == QS_C64;
+    // tangent records only where the tangent form can run (complex64 gauge-Higgs)
+    G.tan_off = (s->lat.gauge_higgs && s->dtype == QS_C64) ? s->tan_off : 0;
+    G.nX0 = s->nX0; G.nX1 = s->nX1;
     G.dt = dt;
-    long long entries = (long long)n * B * (1 + (s->nA + 1) * (s->nB + 1) +
+    long long entries = (long long)n * B * (1 + (G.tan_off ? 2 : 1) * (s->nA + 1) * (s->nB + 1) +
                                             (G.xlut_off ? (s->nXA + 1) * (s->nXB + 1) : 0));
     unsigned blocks = (unsigned)std::min<long long>((entries + 255) / 256, 152 * 16);
     k_build_records<<<blocks, 256, 0, s->stream>>>(G, reinterpret_cast<const DevCouplings *>(s->d_in),
@@ -735,7 +751,7 @@ qs_status build_records(qs_sim *s, size_t op0, size_t n, double dt, int n_steps,
 template <typename R>
 bool merged_schedule(const qs_sim *s) {
     return sizeof(R) == 4 && s->method == 0 && s->xmerge && s->lat.gauge_higgs && s->tmaps_ok &&
-           s->xpass_impl != 1 && s->passes.size() >= 2;
+           s->xpass_impl != 1 && s->passes.size() >= 2 && s->tan_active;
 }
 
 // Factor groups [j0, j1) (records resident from op j0) with shared passes: the last
@@ -778,7 +794,8 @@ qs_status launch_ops_merged(qs_sim *s, const std::vector<Op> &ops, int steps_per
                 carried = true;
                 dir ^= 1;
             } else {
-                if ((st = launch_xpass<R>(s, p, (last && has_z) ? V_ROT_Z : V_ROT, rec, frame)) != QS_OK)
+                if ((st = launch_xpass<R>(s, p, (last && has_z) ? V_ROT_Z : V_ROT, rec, frame, nullptr,
+                                          (last && !has_z) ? 1 : 0)) != QS_OK)
                     return st;
             }
         }
@@ -816,6 +833,20 @@ qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_un
     qs_status st;
     const int B = s->batch;
     const size_t nops = ops.size() / B;
+    // tangent form for complex64 gauge-Higgs TMA passes when every factor group of the
+    // call has |theta| <= pi/4 and C >= 1/2, i.e. (1 + t0^2)^n0 (1 + t1^2)^n1 <= 4:
+    // bounded growth before C is applied, and the scaled Z table u = 1 - C cos phi stays
+    // away from 1, where rounding u would cost relative precision in C
+    s->tan_active = false;
+    if (sizeof(R) == 4 && s->method == 0 && s->lat.gauge_higgs && s->tmaps_ok && s->xpass_impl != 1) {
+        bool ok = true;
+        for (const Op &o : ops) {
+            const double t0 = std::tan(o.thx[0]), t1 = std::tan(o.thx[1]);
+            ok = ok && std::fabs(o.thx[0]) <= 0.25 * M_PI && std::fabs(o.thx[1]) <= 0.25 * M_PI &&
+                 s->nX0 * std::log1p(t0 * t0) + s->nX1 * std::log1p(t1 * t1) <= 2.0 * std::log(2.0);
+        }
+        s->tan_active = ok;
+    }
     if (s->method == 0) {
         if ((st = upload_inputs(s, c, sv, n_steps, path)) != QS_OK) return st;
         if (nops > REC_CHUNK) {
@@ -834,7 +865,8 @@ qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_un
     // private stream; the records it reads are rebuilt in place before every replay.
     const long long key[10] = {(long long)nops, order, n_steps, B, (long long)(uintptr_t)s->state[0],
                                (long long)(uintptr_t)s->d_rec, s->renorm_every,
-                               s->xpass_impl * 16 + s->nbuf + 256 * s->tma_store + 1024 * s->xmerge,
+                               s->xpass_impl * 16 + s->nbuf + 256 * s->tma_store + 1024 * s->xmerge +
+                                   4096 * (int)s->tan_active,
                                s->method, (long long)s->dtype};
     if (!s->graph_exec || memcmp(key, s->graph_key, sizeof(key)) != 0) {
         if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
@@ -1059,6 +1091,9 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
         s->rec_stride += 2 * (s->nXA + 1) * (s->nXB + 1);
         s->max_lut = std::max(s->max_lut, (s->nXA + 1) * (s->nXB + 1));
     }
+    s->tan_off = s->rec_stride;
+    s->rec_stride += 4 + 2 * (s->nA + 1) * (s->nB + 1);   // triple + scaled Z table
+    for (int qb = 0; qb < s->n; ++qb) (s->lat.x_class[qb] ? s->nX1 : s->nX0)++;
     build_passes(s);
     build_variants(s);
     build_tma_passes(s);
@@ -1096,8 +1131,8 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
         cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, dev);
         if (s->sm_count < 1) s->sm_count = 1;
         for (int nb = 2; nb <= 3; ++nb)
-            for (int v = 0; v < 4; ++v)
-                cudaFuncSetAttribute(xpass_tma_kernel(nb, v & 1, (v >> 1) & 1),
+            for (int v = 0; v < 8; ++v)
+                cudaFuncSetAttribute(xpass_tma_kernel(nb, v & 1, (v >> 1) & 1, (v >> 2) & 1),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(s, nb, true));
         int adj64 = (int)(2 * (1 << LT) * 16 + (size_t)(s->nA + 1) * (s->nB + 1) * 16);
         cudaFuncSetAttribute(k_adj_xpass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
@@ -1603,15 +1638,18 @@ qs_status qs_dos(qs_sim *s, double *out) {
     return check_device_flag(s);
 }
 
-qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers, double *best_ms_per_step) {
+qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers, int *best_store,
+                      double *best_ms_per_step) {
     qs_status st;
     if ((st = check_ready(s)) != QS_OK) return st;
     if (n_steps < 1 || n_steps > 1000) FAIL(s, QS_ERR_ARG, "n_steps must be in [1, 1000]");
-    if (!best_xpass || !best_buffers || !best_ms_per_step) FAIL(s, QS_ERR_ARG, "null output");
-    struct Cand { int xpass, nbuf; };
+    if (!best_xpass || !best_buffers || !best_store || !best_ms_per_step) FAIL(s, QS_ERR_ARG, "null output");
+    struct Cand { int xpass, nbuf, store; };
     std::vector<Cand> cands;
-    if (s->dtype == QS_C64 && s->tmaps_ok) { cands.push_back({2, 2}); cands.push_back({2, 3}); }
-    cands.push_back({1, 2});
+    if (s->dtype == QS_C64 && s->tmaps_ok)
+        for (int nb = 2; nb <= 3; ++nb)
+            for (int so = 0; so <= 1; ++so) cands.push_back({2, nb, so});
+    cands.push_back({1, 2, 0});
     const int saved_method = s->method, saved_profile = s->profile, saved_graph = s->use_graph;
     s->method = 0; s->profile = 0; s->use_graph = 0;
     std::vector<qs_couplings> c(s->batch, qs_couplings{1.0, 1.0, 0.6, 0.6});
@@ -1623,7 +1661,7 @@ qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers
     double best = 1e300;
     Cand pick = cands.back();
     for (const Cand &cd : cands) {
-        s->xpass_impl = cd.xpass; s->nbuf = cd.nbuf;
+        s->xpass_impl = cd.xpass; s->nbuf = cd.nbuf; s->tma_store = cd.store;
         if ((st = qs_init_plus(s)) != QS_OK) break;
         if ((st = qs_evolve(s, c.data(), sv.data(), 0.02, 2, 2)) != QS_OK) break;   // warm-up
         CK(s, cudaEventRecord(e0, s->stream));
@@ -1638,8 +1676,9 @@ qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers
     cudaEventDestroy(e1);
     s->method = saved_method; s->profile = saved_profile; s->use_graph = saved_graph;
     if (st != QS_OK) return st;
-    s->xpass_impl = pick.xpass; s->nbuf = pick.nbuf;
-    *best_xpass = pick.xpass; *best_buffers = pick.nbuf; *best_ms_per_step = best / n_steps;
+    s->xpass_impl = pick.xpass; s->nbuf = pick.nbuf; s->tma_store = pick.store;
+    *best_xpass = pick.xpass; *best_buffers = pick.nbuf; *best_store = pick.store;
+    *best_ms_per_step = best / n_steps;
     return QS_OK;
 }
 

@@ -21,6 +21,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -51,6 +52,10 @@ struct TmaPass {
     uint32_t paA_reg[NR], pbA_reg[NR];// parity of stage-A register r (local bits 8..11)
     long long toff_a[8];        // stage A: global offset of thread bit j (local 0..7)
     long long roff_a[NR];       // stage A: global offset of register r (local bits 8..11)
+    int tan_off;                // offset (doubles) of the tangent triple in the record
+    int xscale;                 // tangent form: multiply by the record's C before the
+                                // store (set on the last pass of a group without Z;
+                                // with a Z layer C is in the scaled table)
 };
 
 constexpr int TMA_TILE_BYTES = (1 << LT) * 8;
@@ -218,6 +223,47 @@ __device__ __forceinline__ void rotate_w(u64 (&w)[NR], unsigned mask, const int 
     }
 }
 
+// Tangent form (dev_tan_triple): butterflies a' = a + t b, b' = b - t a on packed
+// register pairs, constants (t, t) and (-t, -t) per class; the cos factors of the whole
+// X layer are applied once, as the record's scalar C.
+struct TanConst { u64 pt[2], nt[2]; };
+
+__device__ __forceinline__ void rotate_t(u64 (&w)[NR], unsigned mask, const int (&cls)[RB], const TanConst &C) {
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+        const bool c = cls[k] != 0;
+        const u64 pt = c ? C.pt[1] : C.pt[0], nt = c ? C.nt[1] : C.nt[0];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (!((r >> k) & 1)) {
+                const int q = r | (1 << k);
+                const u64 a = w[r], b = w[q];
+                w[r] = fma2p(pt, b, a);
+                w[q] = fma2p(nt, a, b);
+            }
+    }
+}
+
+__device__ __forceinline__ void rot_apply(u64 (&w)[NR], unsigned mask, const int (&cls)[RB], const RotConst &C) {
+    rotate_w(w, mask, cls, C);
+}
+__device__ __forceinline__ void rot_apply(u64 (&w)[NR], unsigned mask, const int (&cls)[RB], const TanConst &C) {
+    rotate_t(w, mask, cls, C);
+}
+
+// rotation constants of one operator record, (u, s) or tangent form
+__device__ __forceinline__ void load_xconst(RotConst &C, const double *rec, int) {
+    const float u0 = (float)rec[0], s0 = (float)rec[1], u1 = (float)rec[2], s1 = (float)rec[3];
+    C.nu[0] = pk(-u0, -u0); C.ps[0] = pk(s0, s0); C.ns[0] = pk(-s0, -s0);
+    C.nu[1] = pk(-u1, -u1); C.ps[1] = pk(s1, s1); C.ns[1] = pk(-s1, -s1);
+}
+__device__ __forceinline__ void load_xconst(TanConst &C, const double *rec, int tan_off) {
+    const float t0 = (float)rec[tan_off], t1 = (float)rec[tan_off + 1];
+    C.pt[0] = pk(t0, t0); C.nt[0] = pk(-t0, -t0);
+    C.pt[1] = pk(t1, t1); C.nt[1] = pk(-t1, -t1);
+}
+
 __device__ __forceinline__ void hadamard_w(u64 (&w)[NR], unsigned mask) {
     const u64 one = pk(1.f, 1.f), mone = pk(-1.f, -1.f);
 #pragma unroll
@@ -246,7 +292,8 @@ __device__ __forceinline__ float2 mul_ipow(float2 v, int k) {
 // so consecutive factor groups that take their qubit groups in opposite orders share
 // the pass that holds G (one HBM round trip fewer per Trotter step).  The second round
 // runs stages C, B, A and stores from the stage-A layout.
-template <int NBUF, bool STORE_TMA, bool MERGED>
+// TAN: rotations in the tangent form (records carry the triple at P.tan_off).
+template <int NBUF, bool STORE_TMA, bool MERGED, bool TAN>
 __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__restrict__ psi, const double *__restrict__ recs,
                                                   const double *__restrict__ recs2,
                                                   int rec_stride, int tiles_shift,
@@ -262,7 +309,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
     uint2 *ptab = reinterpret_cast<uint2 *>(lut + (P.apply_z ? (P.nA + 1) * (P.nB + 1) : 0));  // 3 x 256
     __shared__ uint64_t bars[NBUF];
     __shared__ int s_ok;
-    __shared__ RotConst s_rc2;     // MERGED: rotation constants of the second round
+    typedef typename std::conditional<TAN, TanConst, RotConst>::type XC;
+    __shared__ XC s_rc2;           // MERGED: rotation constants of the second round
 
     const int t = threadIdx.x;
     const long long G = gridDim.x;
@@ -336,8 +384,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
     const int nlut = (P.nA + 1) * nB1;
     const bool had = P.hadamard != 0;
     long long cur_batch = -1;
-    float u0 = 0.f, s0 = 0.f, u1 = 0.f, s1 = 0.f;
-    RotConst RC;
+    XC RC;
+    float xs = 1.f;                                   // tangent form: scalar C of the record
     int cls0[RB], cls1[RB], cls2[RB];
 #pragma unroll
     for (int kk = 0; kk < RB; ++kk) {
@@ -354,18 +402,14 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             // operator record of this batch element (angles, phase table)
             __syncthreads();
             const double *rec = recs + batch * rec_stride;
-            u0 = (float)rec[0]; s0 = (float)rec[1]; u1 = (float)rec[2]; s1 = (float)rec[3];
-            RC.nu[0] = pk(-u0, -u0); RC.ps[0] = pk(s0, s0); RC.ns[0] = pk(-s0, -s0);
-            RC.nu[1] = pk(-u1, -u1); RC.ps[1] = pk(s1, s1); RC.ns[1] = pk(-s1, -s1);
-            if (P.apply_z)
+            load_xconst(RC, rec, P.tan_off);
+            if (TAN) xs = (float)rec[P.tan_off + 2];
+            if (P.apply_z) {
+                const int loff = TAN ? P.tan_off + 4 : P.lut_off;   // tangent form: table scaled by C
                 for (int i = t; i < nlut; i += NT)
-                    lut[i] = make_float2((float)rec[P.lut_off + 2 * i], (float)rec[P.lut_off + 2 * i + 1]);
-            if (MERGED && t == 0) {
-                const double *r2 = recs2 + batch * rec_stride;
-                const float v0 = (float)r2[0], w0 = (float)r2[1], v1 = (float)r2[2], w1 = (float)r2[3];
-                s_rc2.nu[0] = pk(-v0, -v0); s_rc2.ps[0] = pk(w0, w0); s_rc2.ns[0] = pk(-w0, -w0);
-                s_rc2.nu[1] = pk(-v1, -v1); s_rc2.ps[1] = pk(w1, w1); s_rc2.ns[1] = pk(-w1, -w1);
+                    lut[i] = make_float2((float)rec[loff + 2 * i], (float)rec[loff + 2 * i + 1]);
             }
+            if (MERGED && t == 0) load_xconst(s_rc2, recs2 + batch * rec_stride, P.tan_off);
             cur_batch = batch;
         }
         if (t == 0) {
@@ -396,7 +440,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                 w[r] = pk(v.x, v.y);
             }
         }
-        if (P.frame & 1) rotate_w(w, P.rot[0], cls0, RC);
+        if (P.frame & 1) rot_apply(w, P.rot[0], cls0, RC);
         else hadamard_w(w, P.rot[0]);
 #pragma unroll
         for (int r = 0; r < NR; ++r) tb[a_base + (r << TB)] = w[r];
@@ -410,7 +454,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                 w[2 * m] = q.x;
                 w[2 * m + 1] = q.y;
             }
-            if (P.frame & 1) rotate_w(w, P.rot[1], cls1, RC);
+            if (P.frame & 1) rot_apply(w, P.rot[1], cls1, RC);
             else hadamard_w(w, P.rot[1]);
 #pragma unroll
             for (int m = 0; m < NR / 2; ++m) tb2[b_base + (m ^ b_x)] = make_ulonglong2(w[2 * m], w[2 * m + 1]);
@@ -419,13 +463,13 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         // ---- stage C: registers = local 4..7; diagonal phase; store ----
 #pragma unroll
         for (int r = 0; r < NR; ++r) w[r] = tb[c_base[r & 7] + (r << 4)];
-        if (P.frame & 1) rotate_w(w, P.rot[2], cls2, RC);
+        if (P.frame & 1) rot_apply(w, P.rot[2], cls2, RC);
         else hadamard_w(w, P.rot[2]);
         // global base of the tile: mid bits -> global c.., upper bits (and batch) -> next+k..
         const long long mid = tile & ((1ll << P.mid_bits) - 1);
         const long long up = tile >> P.mid_bits;
         const long long gbase = (mid << P.c) + (up << (P.next + P.k));
-        if (P.apply_z || (P.frame & 4)) {
+        if (P.apply_z || (P.frame & 4) || (TAN && P.xscale)) {
             float2 v[NR];
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = unpk(w[r]);
@@ -442,6 +486,12 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                     for (int r = 0; r < NR; ++r) { v[r].x *= P.scale; v[r].y *= P.scale; }
                 }
             }
+            if (TAN && !P.apply_z && P.xscale) {
+                // the cos factors of a factor group without Z layer (with a Z layer they
+                // are in its table)
+#pragma unroll
+                for (int r = 0; r < NR; ++r) { v[r].x *= xs; v[r].y *= xs; }
+            }
             if (!MERGED && (P.frame & 4)) {
                 const int k0 = -(__popc(tlo) + __popc(thi) + pc_tile);
 #pragma unroll
@@ -453,8 +503,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         if (MERGED) {
             // ---- second round: stage C (still in registers), B, A; store from A ----
             {
-                const RotConst R2 = s_rc2;
-                rotate_w(w, P.rot[2], cls2, R2);
+                const XC R2 = s_rc2;
+                rot_apply(w, P.rot[2], cls2, R2);
             }
 #pragma unroll
             for (int r = 0; r < NR; ++r) tb[c_base[r & 7] + (r << 4)] = w[r];
@@ -468,8 +518,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                     w[2 * m + 1] = q.y;
                 }
                 {
-                    const RotConst R2 = s_rc2;
-                    rotate_w(w, P.rot[1], cls1, R2);
+                    const XC R2 = s_rc2;
+                    rot_apply(w, P.rot[1], cls1, R2);
                 }
 #pragma unroll
                 for (int m = 0; m < NR / 2; ++m) tb2[b_base + (m ^ b_x)] = make_ulonglong2(w[2 * m], w[2 * m + 1]);
@@ -478,8 +528,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
 #pragma unroll
             for (int r = 0; r < NR; ++r) w[r] = tb[a_base + (r << TB)];
             {
-                const RotConst R2 = s_rc2;
-                rotate_w(w, P.rot[0], cls0, R2);
+                const XC R2 = s_rc2;
+                rot_apply(w, P.rot[0], cls0, R2);
             }
             if (P.frame & 4) {
                 const int k0 = -(__popc(t) + pc_tile);

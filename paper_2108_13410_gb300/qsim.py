@@ -70,7 +70,7 @@ _SIGS = {
     "qs_selftest_wait": ([_P, _D], _I),
     "qs_num_links": ([_P], _I),
     "qs_dos": ([_P, _DP], _I),
-    "qs_autotune": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), _DP], _I),
+    "qs_autotune": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _DP], _I),
     "qs_save": ([_P, ctypes.c_char_p], _I),
     "qs_load": ([_P, ctypes.c_char_p], _I),
     "qs_scan": ([_P, _CP, _I, _DP, _D, _I, _I, _DP], _I),
@@ -266,10 +266,12 @@ def qs_dos(sim, batch: int = 1):
 
 
 def qs_autotune(sim, n_steps: int = 20):
-    """Returns (xpass kernel, tile buffers, ms per step) of the fastest configuration."""
-    xp, nb, ms = _I(), _I(), ctypes.c_double()
-    _check(sim, library().qs_autotune(sim, n_steps, ctypes.byref(xp), ctypes.byref(nb), ctypes.byref(ms)))
-    return xp.value, nb.value, ms.value
+    """Returns (xpass kernel, tile buffers, store mode, ms per step) of the fastest
+    configuration."""
+    xp, nb, so, ms = _I(), _I(), _I(), ctypes.c_double()
+    _check(sim, library().qs_autotune(sim, n_steps, ctypes.byref(xp), ctypes.byref(nb), ctypes.byref(so),
+                                      ctypes.byref(ms)))
+    return xp.value, nb.value, so.value, ms.value
 
 
 def qs_selftest_wait(sim, limit_ms: float):
@@ -430,13 +432,14 @@ class Simulator:
                 table = json.load(open(path))
             except (OSError, ValueError):
                 table = {}
-        if cache and key in table:
-            xp, nb = table[key]["xpass"], table[key]["buffers"]
+        if cache and key in table and "store" in table[key]:
+            xp, nb, so = table[key]["xpass"], table[key]["buffers"], table[key]["store"]
             self.set_option(QS_OPT_XPASS, xp)
             self.set_option(QS_OPT_TMA_BUFFERS, nb)
+            self.set_option(QS_OPT_TMA_STORE, so)
             return table[key]
-        xp, nb, ms = qs_autotune(self.h, n_steps)
-        entry = {"xpass": xp, "buffers": nb, "ms_per_step": ms}
+        xp, nb, so, ms = qs_autotune(self.h, n_steps)
+        entry = {"xpass": xp, "buffers": nb, "store": so, "ms_per_step": ms}
         if cache:
             table[key] = entry
             try:
