@@ -95,12 +95,15 @@ typedef enum {
                                  = two tile buffers in the TMA kernel (default one)  */
     QS_OPT_TMA_STORE = 7,     /* 1 (default): the TMA X pass writes each tile back with
                                  one bulk tensor store; 0: per-thread stores         */
-    QS_OPT_XMERGE = 8         /* 1 (default): complex64 gauge-Higgs runs on the TMA
-                                 kernel let consecutive Trotter factor groups share
-                                 the pass of one qubit group (X of group k, the Z layer
-                                 of k, X of group k+1 on the same qubits; exact because
-                                 all X-type factors commute), so a step takes one pass
-                                 fewer; 0: every factor group takes all its passes    */
+    QS_OPT_XMERGE = 8         /* 1 (default): complex64 runs on the TMA kernel share
+                                 passes.  Gauge-Higgs: consecutive Trotter factor groups
+                                 share the pass of one qubit group (X of group k, the Z
+                                 layer of k, X of group k+1 on the same qubits; exact
+                                 because all X-type factors commute), one pass fewer
+                                 per step.  Unitary gauge: one pass applies H D_X H on
+                                 one qubit group and one applies H, the Z layer and the
+                                 next group's H, two passes fewer per step.  0: every
+                                 factor group takes all its passes                    */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open

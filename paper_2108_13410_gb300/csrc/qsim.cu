@@ -433,12 +433,11 @@ XpassTmaKernel xpass_tma_kernel_nb(bool store_tma, bool merged) {
     return store_tma ? k_xpass_tma<NBUF, true, false, TAN> : k_xpass_tma<NBUF, false, false, TAN>;
 }
 
-// k_xpass_tma instantiation for (buffers, store mode, shared pass, tangent form); shared
-// passes exist in the tangent form only
+// k_xpass_tma instantiation for (buffers, store mode, shared pass, tangent form)
 XpassTmaKernel xpass_tma_kernel(int nbuf, bool store_tma, bool merged, bool tan) {
     if (tan) return nbuf == 3 ? xpass_tma_kernel_nb<3, true>(store_tma, merged)
                               : xpass_tma_kernel_nb<2, true>(store_tma, merged);
-    return nbuf == 3 ? xpass_tma_kernel_nb<3, false>(store_tma, false) : xpass_tma_kernel_nb<2, false>(store_tma, false);
+    return nbuf == 3 ? xpass_tma_kernel_nb<3, false>(store_tma, merged) : xpass_tma_kernel_nb<2, false>(store_tma, merged);
 }
 
 // One X pass.  rec2 != nullptr selects the merged TMA pass: X of the pass's qubits from
@@ -468,7 +467,7 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
         TmaPass P = s->tpasses[NVAR * p + variant];
         P.frame = frame;
         const bool tan = s->tan_active && (frame & 1);
-        if (rec2 && !tan) FAIL(s, QS_ERR_STATE, "shared X pass needs the tangent form");
+        if (rec2 && (frame & 1) && !tan) FAIL(s, QS_ERR_STATE, "shared rotation pass needs the tangent form");
         P.xscale = tan ? xscale : 0;
         size_t sm = tma_smem_bytes(s, s->nbuf, apply_z);
         XpassTmaKernel kern = xpass_tma_kernel(s->nbuf, s->tma_store != 0, rec2 != nullptr, tan);
@@ -806,6 +805,49 @@ qs_status launch_ops_merged(qs_sim *s, const std::vector<Op> &ops, int steps_per
     return QS_OK;
 }
 
+// Unitary gauge with shared passes: the X layer of factor group k is H^n D_X H^n
+// (unnormalised Walsh-Hadamard passes around the Hadamard-basis phase table D_X) and
+// the Z layer is diagonal.  The D_X pass applies H(gx) D_X H(gx) on one qubit group, and
+// the Z pass applies H(gz), the Z layer of group k and the first H(gz) of group k+1, which
+// skips it (all Walsh-Hadamard butterflies on different qubits commute):
+//   [H(gz)]  H(0 .. np-3)  [H(gx) D_X H(gx)]  H(np-3 .. 0)  [H(gz) Z_k H(gz)]
+// with gx = np-1, gz = np-2: 2 np - 2 passes per factor group instead of 2 np.
+template <typename R>
+qs_status launch_ops_merged_ug(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit, size_t j0,
+                               size_t j1) {
+    qs_status st;
+    const int B = s->batch;
+    const size_t nops = ops.size() / B;
+    const int np = (int)s->passes.size();
+    const size_t rs = (size_t)B * s->rec_stride;
+    const int gx = np - 1, gz = np - 2;
+    bool carried = false;   // H(gz) of op k was applied by op k-1's Z pass
+    for (size_t k = j0; k < j1; ++k) {
+        const double *rec = s->d_rec + (k - j0) * rs;
+        const bool has_z = ops[k * B].has_z;
+        if (!carried && (st = launch_xpass<R>(s, gz, V_HAD, rec)) != QS_OK) return st;
+        for (int p = 0; p < np - 2; ++p)
+            if ((st = launch_xpass<R>(s, p, V_HAD, rec)) != QS_OK) return st;
+        if ((st = launch_xpass<R>(s, gx, V_HAD_X, rec, 0, rec)) != QS_OK) return st;   // H D_X H
+        for (int p = np - 3; p >= 0; --p)
+            if ((st = launch_xpass<R>(s, p, V_HAD, rec)) != QS_OK) return st;
+        carried = has_z && k + 1 < j1;
+        if (carried) st = launch_xpass<R>(s, gz, V_HAD_Z, rec, 0, rec + rs);      // H Z_k H(next)
+        else st = launch_xpass<R>(s, gz, has_z ? V_HAD_Z : V_HAD, rec);
+        if (st != QS_OK) return st;
+        if (s->renorm_every > 0 && steps_per_renorm_unit > 0 &&
+            ((k + 1) % ((size_t)s->renorm_every * steps_per_renorm_unit) == 0 || k + 1 == nops))
+            if ((st = renormalise<R>(s)) != QS_OK) return st;
+    }
+    return QS_OK;
+}
+
+template <typename R>
+bool merged_schedule_ug(const qs_sim *s) {
+    return sizeof(R) == 4 && s->method == 0 && s->xmerge && !s->lat.gauge_higgs && s->tmaps_ok &&
+           s->xpass_impl != 1 && s->passes.size() >= 2;
+}
+
 template <typename R>
 qs_status launch_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_unit, size_t j0 = 0,
                      size_t j1 = (size_t)-1) {
@@ -814,6 +856,7 @@ qs_status launch_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm
     const size_t nops = ops.size() / B;
     if (j1 > nops) j1 = nops;
     if (merged_schedule<R>(s)) return launch_ops_merged<R>(s, ops, steps_per_renorm_unit, j0, j1);
+    if (merged_schedule_ug<R>(s)) return launch_ops_merged_ug<R>(s, ops, steps_per_renorm_unit, j0, j1);
     for (size_t k = j0; k < j1; ++k) {
         if (s->method == 0)
             st = run_op_fused<R>(s, &ops[k * B], s->d_rec + (k - j0) * B * (size_t)s->rec_stride, k, nops);

@@ -290,7 +290,9 @@ __device__ __forceinline__ float2 mul_ipow(float2 v, int k) {
 // MERGED: the pass applies X(G) of one factor group, the Z layer, then X(G) of the
 // next factor group (recs2), for the same tile qubits G.  All X-type factors commute,
 // so consecutive factor groups that take their qubit groups in opposite orders share
-// the pass that holds G (one HBM round trip fewer per Trotter step).  The second round
+// the pass that holds G (one HBM round trip fewer per Trotter step).  With Hadamard
+// butterflies (unitary gauge) both rounds are Walsh-Hadamard butterflies on G around
+// the diagonal table (the Hadamard-basis X layer or the Z layer).  The second round
 // runs stages C, B, A and stores from the stage-A layout.
 // TAN: rotations in the tangent form (records carry the triple at P.tan_off).
 template <int NBUF, bool STORE_TMA, bool MERGED, bool TAN>
@@ -502,9 +504,11 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         }
         if (MERGED) {
             // ---- second round: stage C (still in registers), B, A; store from A ----
-            {
+            if (P.frame & 1) {
                 const XC R2 = s_rc2;
                 rot_apply(w, P.rot[2], cls2, R2);
+            } else {
+                hadamard_w(w, P.rot[2]);
             }
 #pragma unroll
             for (int r = 0; r < NR; ++r) tb[c_base[r & 7] + (r << 4)] = w[r];
@@ -517,9 +521,11 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                     w[2 * m] = q.x;
                     w[2 * m + 1] = q.y;
                 }
-                {
+                if (P.frame & 1) {
                     const XC R2 = s_rc2;
                     rot_apply(w, P.rot[1], cls1, R2);
+                } else {
+                    hadamard_w(w, P.rot[1]);
                 }
 #pragma unroll
                 for (int m = 0; m < NR / 2; ++m) tb2[b_base + (m ^ b_x)] = make_ulonglong2(w[2 * m], w[2 * m + 1]);
@@ -527,9 +533,11 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             }
 #pragma unroll
             for (int r = 0; r < NR; ++r) w[r] = tb[a_base + (r << TB)];
-            {
+            if (P.frame & 1) {
                 const XC R2 = s_rc2;
                 rot_apply(w, P.rot[0], cls0, R2);
+            } else {
+                hadamard_w(w, P.rot[0]);
             }
             if (P.frame & 4) {
                 const int k0 = -(__popc(t) + pc_tile);

@@ -125,3 +125,79 @@ def test_shared_passes_at_27_qubits_agree_with_separate_passes():
     scale = np.max(np.abs(amps[1]))
     assert np.max(np.abs(amps[0] - amps[1])) <= 1e-5 * scale
     assert abs(es[0] - es[1]) <= 1e-4
+
+
+@gpu
+@pytest.mark.parametrize("order,n_steps", [(1, 1), (2, 1), (2, 3), (1, 4)])
+@pytest.mark.parametrize("store", [0, 1])
+def test_unitary_gauge_shared_passes_match_oracle(order, n_steps, store):
+    """3x3 torus, unitary gauge (18 link qubits, two passes per Walsh-Hadamard round):
+    a factor group is [H(q0-11) Z H(q0-11)] and [H(q12-17) D_X H(q12-17)], two passes
+    instead of four."""
+    from paper_2108_13410_gb300.qsim import QS_OPT_TMA_STORE
+    lat = OracleLattice(3, 3, True, "ug")
+    c = Couplings(0.3, 0.5, J=0.5, h=0.5)
+    T = 0.2 * n_steps
+    s = O.schedule_linear(T, n_steps)
+    sim = _sim(3, 3, form="ug", dtype="c64")
+    sim.set_option(QS_OPT_TMA_STORE, store)
+    sim.init_plus()
+    sim.evolve([(0.3, 0.5, 0.5, 0.5)], s, T / n_steps, order)
+    _assert_amplitudes(sim.download()[0].numpy(), O.evolve(lat, c, s, T / n_steps, order))
+
+
+@gpu
+def test_unitary_gauge_shared_passes_batch_and_toric_start():
+    """2x5 torus, unitary gauge (20 qubits), batch 2, from the toric-code state psi_1
+    along two different parameter paths."""
+    lat = OracleLattice(2, 5, True, "ug")
+    paths = [[(0.01 * k, 0.3, 0.5, 0.5) for k in range(1, 7)], [(0.2, 0.02 * k, 0.5, 0.5) for k in range(1, 7)]]
+    sim = _sim(2, 5, form="ug", dtype="c64", batch=2)
+    sim.init_toric(0)
+    per_step = [[paths[0][k], paths[1][k]] for k in range(6)]
+    sim.evolve_path(per_step, 0.05, 2)
+    got = sim.download().numpy()
+    psi0 = O.toric_state(lat, 0)
+    for b in range(2):
+        ref = O.evolve_path(lat, [Couplings(g, l, J=J, h=h) for g, l, J, h in paths[b]], 0.05, 2, psi0=psi0)
+        _assert_amplitudes(got[b], ref)
+
+
+@gpu
+def test_unitary_gauge_launch_count():
+    """Unitary gauge 3x3 (two passes per Walsh-Hadamard round): 10 second-order steps =
+    11 factor groups; shared passes: 1 + 2 per group; separate: 4 per group."""
+    from paper_2108_13410_gb300.qsim import QS_OPT_XMERGE
+    sim = _sim(3, 3, form="ug", dtype="c64")
+    sim.init_plus()
+    sim.launch_count()
+    s = O.schedule_linear(1.0, 10)
+    sim.evolve([(0.6, 0.6)], s, 0.1, 2)
+    sim.sync()
+    assert sim.launch_count() == 1 + 1 + 2 * 11      # records + first H pass + 2 per group
+    sim.set_option(QS_OPT_XMERGE, 0)
+    sim.evolve([(0.6, 0.6)], s, 0.1, 2)
+    sim.sync()
+    assert sim.launch_count() == 1 + 4 * 11
+
+
+@gpu
+def test_unitary_gauge_32_qubits_shared_and_separate_passes_agree():
+    """4x4 torus, unitary gauge (32 qubits, four passes per Walsh-Hadamard round: six
+    instead of eight per factor group): three second-order steps with and without
+    shared passes agree on sampled amplitudes."""
+    import torch
+    from paper_2108_13410_gb300.qsim import QS_OPT_XMERGE
+    s = [0.2, 0.4, 0.6]
+    idx = torch.from_numpy(np.random.default_rng(6).integers(0, 1 << 32, 4096))
+    amps = []
+    for merge in (1, 0):
+        sim = _sim(4, 4, form="ug", dtype="c64")
+        sim.set_option(QS_OPT_XMERGE, merge)
+        sim.init_plus()
+        sim.evolve([(0.5, 0.5)], s, 0.1, 2)
+        amps.append(sim.state[0, idx.to(sim.state.device)].cpu().numpy().astype(np.complex128))
+        del sim
+        torch.cuda.empty_cache()
+    scale = np.max(np.abs(amps[1]))
+    assert np.max(np.abs(amps[0] - amps[1])) <= 1e-5 * scale
