@@ -343,6 +343,12 @@ def run_ours(args):
     if rank == 0 and args.adjoint_steps > 0:
         extra["adjoint"] = adjoint_leg(args.adjoint_steps, local, dev, stream)
 
+    if rank == 0 and not args.no_ug32:
+        extra["ug32"] = ug32_leg(local, dev, stream)
+
+    if rank == 0 and not args.no_protocol:
+        extra["protocol"] = protocol_leg(local, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         r, cores, desc = oracle_sample(args.cpu_budget)
@@ -444,6 +450,66 @@ def scan_leg(local, dev, chunk=64):
     return out
 
 
+def ug32_leg(local, dev, stream):
+    """4x4 torus in the unitary gauge: 32 link qubits, complex64 (32 GiB) and complex128
+    (64 GiB) states, (g, lambda) = (0.5, 0.5), J = h = 1, linear ramp T = 20, dt = 0.02,
+    second order; steps from the start of the 1000-step schedule after two warm-up
+    steps.  Reports steps/s, X passes per step and the mean GB/s of each X-pass kernel
+    (2 x state bytes per launch, CUDA events) against the measured HBM peak."""
+    import torch
+    from paper_2108_13410_gb300 import Simulator, QS_OPT_PROFILE, QS_NORM
+    s = linear_midpoints(20.0, 1000)
+    cpl = [(0.5, 0.5)]
+    peak, _ = peaks()
+    out = {"lattice": "4x4 periodic", "form": "unitary gauge", "qubits": 32, "g": 0.5, "lambda": 0.5,
+           "dt": 0.02, "order": 2}
+    for dtype, n in (("c64", 10), ("c128", 2)):
+        sim = Simulator(4, 4, form="ug", dtype=dtype, device=f"cuda:{local}")
+        sim.init_plus()
+        sim.evolve(cpl, s[:2], 0.02, 2)
+        torch.cuda.synchronize(dev)
+        sim.set_option(QS_OPT_PROFILE, 1)
+        sim.profile_read_kinds()
+        sim.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.evolve(cpl, s[2:2 + n], 0.02, 2)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1)
+        kinds = sim.profile_read_kinds()
+        launches = sim.launch_count()
+        sim.set_option(QS_OPT_PROFILE, 0)
+        alg = 2.0 * sim.state_bytes
+        kern = {}
+        for name, (kms, kn) in zip(("plain", "shared"), kinds):
+            if kn:
+                gbs = alg / (kms / kn / 1000.0) / 1e9
+                kern[name] = {"launches": kn, "avg_launch_ms": kms / kn, "achieved_gbs": gbs, "frac": gbs / peak}
+        npass = kinds[0][1] + kinds[1][1]
+        out[dtype] = {"steps": n, "steps_per_s": n / (ms / 1000.0), "ms_per_step": ms / n,
+                      "state_bytes": sim.state_bytes, "passes_per_step": npass / n, "launches": launches,
+                      "xpass": kern, "step_hbm_gbs": npass * alg / (ms / 1000.0) / 1e9,
+                      "norm_minus_1": float(sim.expect(QS_NORM)[0] - 1.0)}
+        del sim
+        torch.cuda.empty_cache()
+    return out
+
+
+def protocol_leg(local, dev):
+    """The hysteresis run of Sec. IV at p = 0.5 on the 3x3 unitary-gauge torus (18
+    qubits, J = h = 1/2, dg = 1e-5, dt = 0.02, second order, complex64): psi_1 carried
+    O -> P -> P' and psi_1' carried O -> P' -> P, 100k steps per state; end energies next
+    to the printed ones."""
+    import torch
+    from paper_2108_13410_gb300.reproduce import hysteresis
+    torch.cuda.synchronize(dev)
+    r = hysteresis(0.5, 1e-5, 0.02)
+    r["steps_per_s"] = 2 * r["steps_per_state"] / r["seconds"]
+    return r
+
+
 def adjoint_leg(n_steps, local, dev, stream):
     """Adjoint-gradient time / forward time on the 27-qubit lattice with the Fourier
     schedule s(t) = t/T + sum_{m<=16} a_m sin(m pi t/T), a_m ~ N(0, 0.01^2) (seed 2108),
@@ -503,6 +569,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-pergate", action="store_true")
+    ap.add_argument("--no-ug32", action="store_true", help="skip the 32-qubit unitary-gauge leg")
+    ap.add_argument("--no-protocol", action="store_true", help="skip the hysteresis-protocol leg")
     ap.add_argument("--source-hash", action="store_true", help="print the X-pass kernel source hash")
     args = ap.parse_args()
     if args.source_hash:

@@ -78,3 +78,17 @@ def test_adjoint_over_more_than_one_record_chunk():
     val, g = sim.adjoint_grad([(0.6, 0.6)], s, T / n, 2)
     assert abs(val[0] - e_ref) <= 1e-9
     np.testing.assert_allclose(jac @ g[0], g_ref, atol=1e-8 * np.max(np.abs(g_ref)) + 1e-12)
+
+
+@gpu
+def test_hysteresis_run_complex64_matches_complex128():
+    """The hysteresis protocol of Sec. IV at p = 0.5 with a coarser dg = 5e-4 (1000 +
+    1000 steps per state): complex64 with renormalisation every 100 steps (the driver's
+    default) gives the complex128 end energies to 5e-6; both lie above the ground energy
+    of the 3x3 unitary-gauge torus at (0, 0.5) and (0.5, 0), which is below -14.0656."""
+    from paper_2108_13410_gb300.reproduce import hysteresis
+    r64 = hysteresis(0.5, 5e-4, 0.02, "c64")
+    r128 = hysteresis(0.5, 5e-4, 0.02, "c128", renorm_every=0)
+    assert abs(r64["E"] - r128["E"]) <= 5e-6
+    assert abs(r64["E_prime"] - r128["E_prime"]) <= 5e-6
+    assert r128["E"] >= -14.065684 and r128["E_prime"] >= -14.065684
