@@ -501,13 +501,18 @@ def protocol_leg(local, dev):
     """The hysteresis run of Sec. IV at p = 0.5 on the 3x3 unitary-gauge torus (18
     qubits, J = h = 1/2, dg = 1e-5, dt = 0.02, second order, complex64): psi_1 carried
     O -> P -> P' and psi_1' carried O -> P' -> P, 100k steps per state; end energies next
-    to the printed ones."""
+    to the printed ones.  Then the broken red paths of Sec. V (r = 0.05, 0.15, 0.25):
+    minimum of d^2E/dg^2 next to the printed one."""
     import torch
-    from paper_2108_13410_gb300.reproduce import hysteresis
+    from paper_2108_13410_gb300.reproduce import hysteresis, red_path_curvature
     torch.cuda.synchronize(dev)
     r = hysteresis(0.5, 1e-5, 0.02)
     r["steps_per_s"] = 2 * r["steps_per_state"] / r["seconds"]
-    return r
+    red = []
+    for rr in (0.05, 0.15, 0.25):
+        c = red_path_curvature(rr)
+        red.append({k: c[k] for k in ("r", "g_min", "printed_g_min", "d2E_min", "steps", "seconds")})
+    return {"hysteresis_p050": r, "red_paths": red}
 
 
 def adjoint_leg(n_steps, local, dev, stream):

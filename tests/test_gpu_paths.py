@@ -92,3 +92,20 @@ def test_hysteresis_run_complex64_matches_complex128():
     assert abs(r64["E"] - r128["E"]) <= 5e-6
     assert abs(r64["E_prime"] - r128["E_prime"]) <= 5e-6
     assert r128["E"] >= -14.065684 and r128["E_prime"] >= -14.065684
+
+
+@gpu
+def test_red_path_curvature_minima():
+    """The broken red paths of Sec. V (psi_1 carried to R(0.5, r), then along lambda = r
+    from g = 0.5 to 0; dg = 1e-5, dt = 0.02, second order, complex64 renormalised every 100
+    steps): the minimum of d^2E/dg^2 of the adiabatic energy lies within 0.003 of the
+    oracle's ground-energy curvature minimum (tests/golden/red_path_curvature.txt) and
+    within 0.004 of the minimum printed in the paper."""
+    import os
+    from paper_2108_13410_gb300.reproduce import red_path_curvature
+    path = os.path.join(os.path.dirname(__file__), "golden", "red_path_curvature.txt")
+    rows = [[float(x) for x in l.split()] for l in open(path) if l.strip() and not l.startswith("#")]
+    for r, g_ed, _, printed in rows:
+        out = red_path_curvature(r)
+        assert abs(out["g_min"] - g_ed) <= 0.003, (r, out["g_min"], g_ed)
+        assert abs(out["g_min"] - printed) <= 0.004, (r, out["g_min"], printed)
