@@ -177,7 +177,18 @@ def qs_init_toric(sim, which: int):
 
 def qs_evolve_path(sim, per_step, dt: float, order: int, batch: int = 1):
     """per_step: sequence of n_steps coupling records (batch 1) or of n_steps lists of
-    `batch` records; step k evolves under H1 with those couplings."""
+    `batch` records; step k evolves under H1 with those couplings.  A float64 numpy array
+    of shape (n_steps * batch, 4) with columns (g, lambda, J, h), step-major, is passed
+    without a per-record Python loop."""
+    if hasattr(per_step, "shape") and hasattr(per_step, "dtype"):
+        import numpy as np
+        a = np.asarray(per_step, dtype=np.float64)
+        if a.ndim != 2 or a.shape[1] != 4 or a.shape[0] % batch:
+            raise ValueError("per-step coupling array must have shape (n_steps * batch, 4)")
+        rec = np.ascontiguousarray(a[:, [2, 3, 0, 1]])          # qs_couplings layout {J, h, g, lambda}
+        arr = rec.ctypes.data_as(ctypes.POINTER(qs_couplings))
+        _check(sim, library().qs_evolve_path(sim, arr, dt, a.shape[0] // batch, order))
+        return
     flat = []
     for rec in per_step:
         if batch == 1:

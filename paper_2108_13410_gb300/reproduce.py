@@ -2,7 +2,7 @@
 on the GPU.
 
     python -m paper_2108_13410_gb300.reproduce [--p 0.12 0.50] [--dg 1e-5] [--dt 0.02]
-                                               [--red 0.05 0.15 0.25]
+                                               [--red 0.05 0.15 0.25] [--table1]
 
 3x3 torus, unitary-gauge form (18 link qubits), J = h = 1/2.  E: psi_1 prepared at O is
 carried along the g axis to P(p, 0), then along the blue path to P'(0, p); E': psi_1'
@@ -99,6 +99,60 @@ def red_path_curvature(r: float, p: float = 0.5, dg: float = 1e-5, dt: float = 0
     return out
 
 
+PRINTED_TABLE1 = {200: (0.03982, 4.79e-5), 500: (0.04009, 4.99e-5), 800: (0.04075, 4.98e-5)}
+
+
+def trotter_error_study(ns=(10, 200, 500, 800), n0: int = 10, r: float = 0.05, p: float = 0.5,
+                        grid: float = 1e-4, dtype: str = "c64", order: int = 2, renorm_every: int = 100):
+    """The Trotter-error comparison of Sec. VI (Table I) on the subpath R(p, r) -> R'(0, r).
+
+    Reading: the state is prepared once at R (psi_1 carried O -> P -> R with dg = 1e-5,
+    dt = 0.02), then every run n takes the subpath with dg = 1e-4 / n and dt = 0.2 / n, so
+    dg / dt is the same for all n (the same continuous adiabatic path) and the runs differ
+    by their Trotter error only.  E_n(g) = <H1(g, r)> is sampled every `grid` in g (the
+    same points for every n); delta_n = sum over the samples of |E_n0(g) - E_n(g)| and
+    alpha_n = max over the samples.  3x3 torus, unitary gauge, J = h = 1/2.  The
+    differences are ~1e-6: complex64 rounding (~3e-6 over these runs) hides them, so the
+    comparison needs complex128."""
+    import numpy as np
+    from . import Simulator, QS_OPT_RENORM_EVERY
+    from .protocol import prepare, segment
+    t0 = time.perf_counter()
+    sim = Simulator(3, 3, form="ug", dtype=dtype)
+    sim.set_option(QS_OPT_RENORM_EVERY, renorm_every)
+    sim.init_toric(0)
+    sim.evolve_path(prepare(p, 1e-5, "g"), 0.02, order)
+    sim.evolve_path(segment((p, 0.0), (p, r), 1e-5), 0.02, order)
+    at_r = sim.state.clone()
+    n_pts = int(round(p / grid))
+    curves, runs = {}, []
+    for n in ns:
+        dg, dt = 1e-4 / n, 0.2 / n
+        per = int(round(grid / dg))                 # steps between samples
+        sim.state.copy_(at_r)
+        t1 = time.perf_counter()
+        e = np.empty(n_pts)
+        for j in range(n_pts):
+            k = j * per + np.arange(1, per + 1)     # global step indices of this piece
+            a = np.empty((per, 4))
+            a[:, 0] = p - dg * k                    # g_k = p - k dg
+            a[:, 1] = r
+            a[:, 2] = 0.5
+            a[:, 3] = 0.5
+            sim.evolve_path(a, dt, order)
+            e[j] = float(sim.energy([(a[-1, 0], r, 0.5, 0.5)])[0])
+        curves[n] = e
+        runs.append({"n": n, "dg": dg, "dt": dt, "steps": per * n_pts, "seconds": time.perf_counter() - t1})
+    for run in runs:
+        d = np.abs(curves[n0] - curves[run["n"]])
+        run["delta"] = float(d.sum())
+        run["alpha"] = float(d.max())
+        if run["n"] in PRINTED_TABLE1:
+            run["printed_delta"], run["printed_alpha"] = PRINTED_TABLE1[run["n"]]
+    return {"r": r, "p": p, "n0": n0, "grid": grid, "samples": n_pts, "dtype": dtype, "runs": runs,
+            "seconds": time.perf_counter() - t0}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--p", type=float, nargs="+", default=[0.12, 0.50])
@@ -108,12 +162,16 @@ def main():
     ap.add_argument("--renorm-every", type=int, default=100)
     ap.add_argument("--red", type=float, nargs="*", default=[],
                     help="also the second-derivative minima along the red paths at these r")
+    ap.add_argument("--table1", action="store_true",
+                    help="also the Trotter-error comparison of Sec. VI (n = 10, 200, 500, 800; complex128)")
     a = ap.parse_args()
     out = {"hysteresis": [hysteresis(p, a.dg, a.dt, a.dtype, renorm_every=a.renorm_every) for p in a.p],
            "dg": a.dg, "dt": a.dt, "dtype": a.dtype}
     if a.red:
         out["red_paths"] = [red_path_curvature(r, dg=a.dg, dt=a.dt, dtype=a.dtype, renorm_every=a.renorm_every)
                             for r in a.red]
+    if a.table1:
+        out["table1"] = trotter_error_study(grid=1e-5, dtype="c128", renorm_every=0)
     print(json.dumps(out))
 
 

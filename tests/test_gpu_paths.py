@@ -109,3 +109,17 @@ def test_red_path_curvature_minima():
         out = red_path_curvature(r)
         assert abs(out["g_min"] - g_ed) <= 0.003, (r, out["g_min"], g_ed)
         assert abs(out["g_min"] - printed) <= 0.004, (r, out["g_min"], printed)
+
+
+@gpu
+def test_trotter_error_study_scales_as_second_order():
+    """The Sec. VI comparison on a short subpath (R(0.1, 0.05) -> R'(0, 0.05), complex128):
+    runs with dg = 1e-4/n, dt = 0.2/n follow the same continuous path, so E_10 - E_n is
+    the Trotter error of the n = 10 run minus that of run n; for a second-order product
+    it scales as 1 - (10/n)^2, so delta_20 / delta_40 = 0.75 / 0.9375 = 0.8."""
+    from paper_2108_13410_gb300.reproduce import trotter_error_study
+    out = trotter_error_study(ns=(10, 20, 40), p=0.1, grid=1e-3, dtype="c128", renorm_every=0)
+    d = {run["n"]: run for run in out["runs"]}
+    assert d[10]["delta"] == 0.0
+    assert 0.72 <= d[20]["delta"] / d[40]["delta"] <= 0.88
+    assert 0.0 < d[40]["alpha"] < 1e-5
