@@ -92,7 +92,8 @@ typedef enum {
                                  2 (three CTAs per SM) or 3 (default; two CTAs per SM) */
     QS_OPT_ADJOINT = 6,       /* complex64 adjoint reverse pass: bit 0 set = register-
                                  staged kernel, clear = TMA kernel (default); bit 1 set
-                                 = two tile buffers in the TMA kernel (default one)  */
+                                 = one tile buffer in the TMA kernel (two CTAs per SM),
+                                 clear = two buffers (default)                        */
     QS_OPT_TMA_STORE = 7,     /* 1 (default): the TMA X pass writes each tile back with
                                  one bulk tensor store; 0: per-thread stores         */
     QS_OPT_XMERGE = 8         /* 1 (default): complex64 runs on the TMA kernel share

@@ -46,7 +46,53 @@ __device__ __forceinline__ void adj_rotate_w(u64 (&p)[NR], u64 (&l)[NR], unsigne
     }
 }
 
-template <int NBUF>
+// Tangent form (records from dev_tan_triple): the inverse factor is cos th [[1, -t],
+// [t, 1]]; C = prod cos th is applied first (with the inverse Z layer, through the
+// conjugated scaled table, or alone for a group without Z), so when stage s reads its
+// terms psi and lambda both still carry prod cos th over the X qubits not yet
+// un-rotated; corr = prod (1 + t^2) over those qubits (= 1 / that product squared)
+// restores the terms.  corr is the value at the start of the stage and drops by
+// qi = 1 / (1 + t^2) of each qubit the stage un-rotates before reading the next one.
+// The pair products are accumulated as packed FP32x2 FMAs.
+__device__ __forceinline__ void adj_rotate_t(u64 (&p)[NR], u64 (&l)[NR], unsigned mask, const int (&cls)[RB],
+                                             const TanConst &C, float corr, float qi0, float qi1, float &g0,
+                                             float &g1) {
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+        const bool c = cls[k] != 0;
+        const u64 pt = c ? C.pt[1] : C.pt[0], nt = c ? C.nt[1] : C.nt[0];
+        u64 accp = 0ull, accm = 0ull;   // (+0.0f, +0.0f)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if ((r >> k) & 1) continue;
+            const int q = r | (1 << k);
+            accp = fma2p(l[q], p[r], accp);
+            accm = fma2p(l[r], p[q], accm);
+            const u64 pa = p[r], pb = p[q], la = l[r], lb = l[q];
+            p[r] = fma2p(nt, pb, pa);
+            p[q] = fma2p(pt, pa, pb);
+            l[r] = fma2p(nt, lb, la);
+            l[q] = fma2p(pt, la, lb);
+        }
+        const float2 sp = unpk(accp), sm = unpk(accm);
+        const float g = ((sp.x + sp.y) - (sm.x + sm.y)) * corr;
+        if (c) g1 += g; else g0 += g;
+        corr *= c ? qi1 : qi0;
+    }
+}
+
+__device__ __forceinline__ void adj_rotate(u64 (&p)[NR], u64 (&l)[NR], unsigned mask, const int (&cls)[RB],
+                                           const RotConst &C, float, float, float, float &g0, float &g1) {
+    adj_rotate_w(p, l, mask, cls, C, g0, g1);
+}
+__device__ __forceinline__ void adj_rotate(u64 (&p)[NR], u64 (&l)[NR], unsigned mask, const int (&cls)[RB],
+                                           const TanConst &C, float corr, float qi0, float qi1, float &g0,
+                                           float &g1) {
+    adj_rotate_t(p, l, mask, cls, C, corr, qi0, qi1, g0, g1);
+}
+
+template <int NBUF, bool TAN>
 __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__restrict__ psi, float2 *__restrict__ lam,
                                                    const double *__restrict__ recs, int rec_stride, int tiles_shift,
                                                    int *__restrict__ err_flag, double *__restrict__ partials,
@@ -124,7 +170,11 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
     }
     const long long tmask = (1ll << tiles_shift) - 1;
     long long cur_batch = -1;
-    RotConst RC;
+    typedef typename std::conditional<TAN, TanConst, RotConst>::type XC;
+    XC RC;
+    float corr[3] = {1.f, 1.f, 1.f};
+    float qi0 = 1.f, qi1 = 1.f;     // 1 / (1 + t^2) per class
+    float xs = 1.f;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
 
     long long tile = first;
@@ -150,11 +200,21 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
             }
             __syncthreads();
             const double *rec = recs + batch * rec_stride;
-            const float u0 = (float)rec[0], s0 = (float)rec[1], u1 = (float)rec[2], s1 = (float)rec[3];
-            RC.nu[0] = pk(-u0, -u0); RC.ps[0] = pk(s0, s0); RC.ns[0] = pk(-s0, -s0);
-            RC.nu[1] = pk(-u1, -u1); RC.ps[1] = pk(s1, s1); RC.ns[1] = pk(-s1, -s1);
-            if (zinv)   // inverse Z layer: conjugated phase table
-                for (int i = t; i < nlut; i += NT) lut[i] = make_float2((float)rec[4 + 2 * i], -(float)rec[5 + 2 * i]);
+            load_xconst(RC, rec, P.tan_off);
+            if (TAN) {
+                const double q0 = 1.0 + rec[P.tan_off] * rec[P.tan_off];
+                const double q1 = 1.0 + rec[P.tan_off + 1] * rec[P.tan_off + 1];
+                for (int st = 0; st < 3; ++st)
+                    corr[st] = (float)(pow(q0, (double)P.adj_u[st][0]) * pow(q1, (double)P.adj_u[st][1]));
+                qi0 = (float)(1.0 / q0);
+                qi1 = (float)(1.0 / q1);
+                xs = (float)rec[P.tan_off + 2];
+            }
+            if (zinv) {   // inverse Z layer: conjugated phase table (tangent form: scaled by C)
+                const int loff = TAN ? P.tan_off + 4 : 4;
+                for (int i = t; i < nlut; i += NT)
+                    lut[i] = make_float2((float)rec[loff + 2 * i], -(float)rec[loff + 2 * i + 1]);
+            }
             cur_batch = batch;
         }
         if (NBUF == 1) {
@@ -197,6 +257,14 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
                 l[r] = pk(vl.x, vl.y);
             }
         }
+        if (TAN && !zinv && P.xscale) {   // C of a factor group without Z layer
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const float2 vp = unpk(p[r]), vl = unpk(l[r]);
+                p[r] = pk(vp.x * xs, vp.y * xs);
+                l[r] = pk(vl.x * xs, vl.y * xs);
+            }
+        }
         if (P.frame & 2) {
             const int k0 = __popc(t) + pc_tile;
 #pragma unroll
@@ -206,7 +274,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
                 l[r] = pk(vl.x, vl.y);
             }
         }
-        adj_rotate_w(p, l, P.rot[0], cls0, RC, g0, g1);
+        adj_rotate(p, l, P.rot[0], cls0, RC, corr[0], qi0, qi1, g0, g1);
 #pragma unroll
         for (int r = 0; r < NR; ++r) { tp[a_base + (r << TB)] = p[r]; tl[a_base + (r << TB)] = l[r]; }
         __syncthreads();
@@ -219,7 +287,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
                 p[2 * m] = qp.x; p[2 * m + 1] = qp.y;
                 l[2 * m] = ql.x; l[2 * m + 1] = ql.y;
             }
-            adj_rotate_w(p, l, P.rot[1], cls1, RC, g0, g1);
+            adj_rotate(p, l, P.rot[1], cls1, RC, corr[1], qi0, qi1, g0, g1);
 #pragma unroll
             for (int m = 0; m < NR / 2; ++m) {
                 tp2[b_base + (m ^ b_x)] = make_ulonglong2(p[2 * m], p[2 * m + 1]);
@@ -230,7 +298,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
         // ---- stage C ----
 #pragma unroll
         for (int r = 0; r < NR; ++r) { p[r] = tp[c_base[r & 7] + (r << 4)]; l[r] = tl[c_base[r & 7] + (r << 4)]; }
-        adj_rotate_w(p, l, P.rot[2], cls2, RC, g0, g1);
+        adj_rotate(p, l, P.rot[2], cls2, RC, corr[2], qi0, qi1, g0, g1);
         if (P.frame & 4) {
             const int k0 = -(__popc(tlo) + __popc(thi) + pc_tile);
 #pragma unroll

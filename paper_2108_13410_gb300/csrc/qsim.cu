@@ -85,7 +85,7 @@ struct qs_sim {
     // persistent TMA X pass (complex64)
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
     int nbuf = 3;                          // TMA shared-memory buffers per CTA (2 or 3)
-    int adj_nbuf = 1;                      // tile buffers of the TMA adjoint pass (1 or 2)
+    int adj_nbuf = 2;                      // tile buffers of the TMA adjoint pass (1 or 2)
     int tma_store = 1;                     // X pass writes tiles back with TMA stores
     int xmerge = 1;                        // share the pass of one qubit group between factor groups
     int tan_off = 0;                       // tangent triple in the operator record
@@ -438,6 +438,15 @@ XpassTmaKernel xpass_tma_kernel(int nbuf, bool store_tma, bool merged, bool tan)
     if (tan) return nbuf == 3 ? xpass_tma_kernel_nb<3, true>(store_tma, merged)
                               : xpass_tma_kernel_nb<2, true>(store_tma, merged);
     return nbuf == 3 ? xpass_tma_kernel_nb<3, false>(store_tma, merged) : xpass_tma_kernel_nb<2, false>(store_tma, merged);
+}
+
+typedef void (*AdjKernel)(float2 *, float2 *, const double *, int, int, int *, double *, int, int, int,
+                          const CUtensorMap, const CUtensorMap, const TmaPass);
+
+// k_adj_tma instantiation for (tile buffers, tangent form)
+AdjKernel adj_tma_kernel(int nbuf, bool tan) {
+    if (nbuf == 1) return tan ? k_adj_tma<1, true> : k_adj_tma<1, false>;
+    return tan ? k_adj_tma<2, true> : k_adj_tma<2, false>;
 }
 
 // One X pass.  rec2 != nullptr selects the merged TMA pass: X of the pass's qubits from
@@ -995,10 +1004,13 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
     const bool use_tma = sizeof(R) == 4 && s->tmaps_ok && s->tmaps_aux_ok && s->adj_impl != 1;
     const size_t adj_smem = 2 * (size_t)TMA_TILE_BYTES * s->adj_nbuf + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8;
     unsigned Gt = 1;
+    // tangent form in the reverse sweep whenever the forward of this call used it (same
+    // factor groups, so the same angle checks hold)
+    const bool adj_tan = use_tma && s->tan_active;
+    const AdjKernel adj_kern = adj_tma_kernel(s->adj_nbuf, adj_tan);
     if (use_tma) {
         int per_sm = 0;
-        if (s->adj_nbuf == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_tma<1>, NT, adj_smem);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_tma<2>, NT, adj_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_kern, NT, adj_smem);
         if (per_sm < 1) per_sm = 1;
         Gt = (unsigned)std::min<long long>((long long)B << (s->n - LT), (long long)per_sm * s->sm_count);
     }
@@ -1019,23 +1031,27 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
         const double *rec = s->d_rec + (jj - chunk0) * B * (size_t)s->rec_stride;
         if (use_tma) {
             CK(s, cudaMemsetAsync(s->d_adj_part, 0, nblk_t * B * RED_NV * sizeof(double), s->stream));
+            int done[2] = {0, 0};   // X qubits per class already un-rotated in this factor group
             for (int pi = 0; pi < np; ++pi) {
                 const int p = np - 1 - pi;
                 TmaPass P = s->tpasses[NVAR * p + V_ROT];
                 P.frame = 1 | ((jj + 1 == nops && pi == 0) ? 2 : 0) | ((jj == 0 && pi == np - 1) ? 4 : 0);
                 const int zinv = (pi == 0 && ops[jj * B].has_z) ? 1 : 0;
-                if (s->adj_nbuf == 1)
-                    k_adj_tma<1><<<Gt, NT, adj_smem, s->stream>>>((float2 *)s->state[0], (float2 *)s->state[1], rec,
-                                                                s->rec_stride, s->n - LT, s->d_err, s->d_adj_part,
-                                                                (int)nblk_t, pi * (int)Gt, zinv, s->tmaps[p],
-                                                                s->tmaps_aux[p], P);
-                else
-                    k_adj_tma<2><<<Gt, NT, adj_smem, s->stream>>>((float2 *)s->state[0], (float2 *)s->state[1], rec,
-                                                                s->rec_stride, s->n - LT, s->d_err, s->d_adj_part,
-                                                                (int)nblk_t, pi * (int)Gt, zinv, s->tmaps[p],
-                                                                s->tmaps_aux[p], P);
+                P.xscale = (adj_tan && pi == 0 && !ops[jj * B].has_z) ? 1 : 0;
+                for (int stg = 0; stg < 3; ++stg) {          // stages run A, B, C
+                    P.adj_u[stg][0] = s->nX0 - done[0];
+                    P.adj_u[stg][1] = s->nX1 - done[1];
+                    for (int kk = 0; kk < RB; ++kk)
+                        if ((P.rot[stg] >> kk) & 1u) done[(P.cls[stg] >> kk) & 1u]++;
+                }
+                adj_kern<<<Gt, NT, adj_smem, s->stream>>>((float2 *)s->state[0], (float2 *)s->state[1], rec,
+                                                          s->rec_stride, s->n - LT, s->d_err, s->d_adj_part,
+                                                          (int)nblk_t, pi * (int)Gt, zinv, s->tmaps[p],
+                                                          s->tmaps_aux[p], P);
                 CKL(s); s->launches++;
             }
+            if (done[0] != s->nX0 || done[1] != s->nX1)
+                FAIL(s, QS_ERR_STATE, "reverse passes do not cover every X qubit once");
             k_finish<<<B, RED_THREADS, 0, s->stream>>>(s->d_adj_part, (int)nblk_t, 4, s->d_grad + jj * B * RED_NV);
             CKL(s); s->launches++;
             continue;
@@ -1183,10 +1199,12 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
         cudaFuncSetAttribute(k_apply_h_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_apply_h_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_xmeasure<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1 << LT) * 16));
-        cudaFuncSetAttribute(k_adj_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(4 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
-        cudaFuncSetAttribute(k_adj_tma<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(2 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
+        for (int tn = 0; tn <= 1; ++tn) {
+            cudaFuncSetAttribute(adj_tma_kernel(2, tn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(4 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
+            cudaFuncSetAttribute(adj_tma_kernel(1, tn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(2 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
+        }
     }
     size_t smem64 = (size_t)(1 << LT) * 16 + (size_t)s->max_lut * 16;
     cudaFuncSetAttribute(k_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
@@ -1271,7 +1289,7 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
         case QS_OPT_ADJOINT:
             if (value < 0 || value > 3) FAIL(s, QS_ERR_ARG, "adjoint option must be 0..3");
             s->adj_impl = (value & 1) ? 1 : 0;
-            s->adj_nbuf = (value & 2) ? 2 : 1;
+            s->adj_nbuf = (value & 2) ? 1 : 2;
             return QS_OK;
         case QS_OPT_TMA_BUFFERS:
             if (value != 2 && value != 3) FAIL(s, QS_ERR_ARG, "TMA buffers must be 2 or 3");

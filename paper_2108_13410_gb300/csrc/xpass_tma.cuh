@@ -56,6 +56,8 @@ struct TmaPass {
     int xscale;                 // tangent form: multiply by the record's C before the
                                 // store (set on the last pass of a group without Z;
                                 // with a Z layer C is in the scaled table)
+    int adj_u[3][2];            // adjoint, tangent form: X qubits of the factor group per
+                                // class not yet un-rotated when stage s reads its terms
 };
 
 constexpr int TMA_TILE_BYTES = (1 << LT) * 8;

@@ -137,3 +137,28 @@ def test_batched_complex64_adjoint_tma_path(L):
     psi0 = sim.download().numpy().astype(np.complex128)
     for b in range(2):
         assert np.linalg.norm(psi0[b] - O.plus_state(lat.n_qubits)) <= 1e-4
+
+
+@gpu
+@pytest.mark.parametrize("T,n", [(2.0, 16), (8.0, 8)])
+@pytest.mark.parametrize("adj", [0, 2])
+def test_complex64_adjoint_forms_and_buffers(T, n, adj):
+    """complex64 adjoint on the 3x2 torus in both forms of the reverse pass: small angles
+    (T = 2, 16 steps) run the tangent form, large angles (T = 8, 8 steps: X angles
+    near 1) the (u, s) rotations; with two and one tile buffers (QS_OPT_ADJOINT 0, 2).
+    Gradient within 1e-3 of the largest oracle component, value within 1e-4 relative,
+    psi uncomputed back to |+> within 1e-4."""
+    from paper_2108_13410_gb300.qsim import QS_OPT_ADJOINT
+    lat = OracleLattice(3, 2, True, "gh")
+    c = Couplings(0.6, 0.6)
+    s = O.schedule_fourier(T, n, synth.fourier_coeffs(4, seed=7, std=0.05))
+    e_ref, g_ref = O.energy_gradient(lat, c, s, T / n, 2, np.eye(n))
+    sim = _sim(3, 2, form="gh", dtype="c64", aux=True)
+    sim.set_option(QS_OPT_ADJOINT, adj)
+    for _ in range(2):                       # twice in a row: nothing left over between calls
+        sim.init_plus()
+        val, g = sim.adjoint_grad([(0.6, 0.6)], s, T / n, 2)
+        assert abs(val[0] - e_ref) <= 1e-4 * abs(e_ref)
+        _close(g[0], g_ref, 1e-3)
+        psi0 = sim.download()[0].numpy().astype(np.complex128)
+        assert np.linalg.norm(psi0 - O.plus_state(lat.n_qubits)) <= 1e-4
