@@ -96,7 +96,7 @@ typedef enum {
                                  clear = two buffers (default)                        */
     QS_OPT_TMA_STORE = 7,     /* 1 (default): the TMA X pass writes each tile back with
                                  one bulk tensor store; 0: per-thread stores         */
-    QS_OPT_XMERGE = 8         /* 1 (default): complex64 runs on the TMA kernel share
+    QS_OPT_XMERGE = 8,        /* 1 (default): complex64 runs on the TMA kernel share
                                  passes.  Gauge-Higgs: consecutive Trotter factor groups
                                  share the pass of one qubit group (X of group k, the Z
                                  layer of k, X of group k+1 on the same qubits; exact
@@ -105,6 +105,11 @@ typedef enum {
                                  one qubit group and one applies H, the Z layer and the
                                  next group's H, two passes fewer per step.  0: every
                                  factor group takes all its passes                    */
+    QS_OPT_PDL = 9            /* 1 (default): the TMA X passes are launched with
+                                 programmatic stream serialisation, so a pass is
+                                 scheduled and sets up while the previous kernel
+                                 drains and waits for its writes before reading
+                                 global memory; 0: plain stream order             */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open

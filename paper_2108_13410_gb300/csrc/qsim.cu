@@ -88,6 +88,7 @@ struct qs_sim {
     int adj_nbuf = 2;                      // tile buffers of the TMA adjoint pass (1 or 2)
     int tma_store = 1;                     // X pass writes tiles back with TMA stores
     int xmerge = 1;                        // share the pass of one qubit group between factor groups
+    int pdl = 1;                           // X passes launched with programmatic stream serialisation
     int tan_off = 0;                       // tangent triple in the operator record
     int nX0 = 0, nX1 = 0;                  // X qubits per class
     bool tan_active = false;               // this call's X passes use the tangent form
@@ -484,8 +485,20 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm);
         if (per_sm < 1) per_sm = 1;
         long long g = std::min<long long>(P.total_tiles, (long long)per_sm * s->sm_count);
-        kern<<<(unsigned)g, NT, sm, s->stream>>>((float2 *)s->state[0], rec, rec2 ? rec2 : rec, s->rec_stride,
-                                               s->n - LT, s->d_err, s->tmaps[p], P);
+        // programmatic dependent launch: the pass may be scheduled while the previous
+        // kernel drains; it waits (griddepcontrol.wait) before reading global memory
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)g);
+        cfg.blockDim = dim3(NT);
+        cfg.dynamicSmemBytes = sm;
+        cfg.stream = s->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = s->pdl ? 1 : 0;
+        CK(s, cudaLaunchKernelEx(&cfg, kern, (float2 *)s->state[0], rec, rec2 ? rec2 : rec, s->rec_stride,
+                                 s->n - LT, s->d_err, s->tmaps[p], P));
     } else {
         if (rec2) FAIL(s, QS_ERR_STATE, "merged X pass needs the TMA kernel");
         k_xpass<R><<<grid, NT, smem, s->stream>>>((V<R> *)s->state[0], s->dim, rec, s->rec_stride,
@@ -918,7 +931,7 @@ qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_un
     const long long key[10] = {(long long)nops, order, n_steps, B, (long long)(uintptr_t)s->state[0],
                                (long long)(uintptr_t)s->d_rec, s->renorm_every,
                                s->xpass_impl * 16 + s->nbuf + 256 * s->tma_store + 1024 * s->xmerge +
-                                   4096 * (int)s->tan_active,
+                                   4096 * (int)s->tan_active + 8192 * s->pdl,
                                s->method, (long long)s->dtype};
     if (!s->graph_exec || memcmp(key, s->graph_key, sizeof(key)) != 0) {
         if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
@@ -1286,6 +1299,8 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
             s->tma_store = value != 0; return QS_OK;
         case QS_OPT_XMERGE:
             s->xmerge = value != 0; return QS_OK;
+        case QS_OPT_PDL:
+            s->pdl = value != 0; return QS_OK;
         case QS_OPT_ADJOINT:
             if (value < 0 || value > 3) FAIL(s, QS_ERR_ARG, "adjoint option must be 0..3");
             s->adj_impl = (value & 1) ? 1 : 0;

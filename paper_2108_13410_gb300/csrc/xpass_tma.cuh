@@ -341,6 +341,12 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         }
     }
     __syncthreads();
+    // Programmatic dependent launch: the next pass may start its set-up (everything above
+    // reads only kernel parameters), and this one waits for the previous kernel's writes
+    // (the state, the operator records) before its first read of global memory.  Both
+    // instructions do nothing when the launch carries no programmatic dependency.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     auto coords_of = [&](long long tile, int &x1, int &x2, int &x4) {
         x1 = 0;

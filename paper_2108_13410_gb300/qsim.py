@@ -23,7 +23,7 @@ QS_GAUGE_HIGGS, QS_UNITARY_GAUGE = 0, 1
 QS_C64, QS_C128 = 0, 1
 QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
 QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_ADJOINT, \
-    QS_OPT_TMA_STORE, QS_OPT_XMERGE = range(9)
+    QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL = range(10)
 
 
 class QsError(RuntimeError):

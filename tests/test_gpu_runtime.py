@@ -180,3 +180,23 @@ def test_energy_from_tiled_x_measurement_matches_oracle():
     sim.init_plus()
     sim.evolve([(0.6, 0.6)], s27, 0.02, 2)
     assert abs(sim.energy([(0.6, 0.6)])[0] - O.energy(ref27, ug, Couplings(0.6, 0.6))) <= 2 * 50 * 1e-5
+
+
+@gpu
+@pytest.mark.parametrize("form,L", [("gh", (3, 3)), ("ug", (3, 3))])
+def test_programmatic_dependent_launch_changes_nothing(form, L):
+    """QS_OPT_PDL only lets an X pass be scheduled while the previous kernel drains (it
+    waits for that kernel's writes before reading global memory): results with and without
+    it are bit-identical, with renormalisation kernels in between."""
+    from paper_2108_13410_gb300 import QS_OPT_RENORM_EVERY
+    from paper_2108_13410_gb300.qsim import QS_OPT_PDL
+    s = O.schedule_linear(2.0, 40)
+    out = []
+    for pdl in (1, 0):
+        sim = _sim(*L, form=form, dtype="c64")
+        sim.set_option(QS_OPT_PDL, pdl)
+        sim.set_option(QS_OPT_RENORM_EVERY, 7)
+        sim.init_plus()
+        sim.evolve([(0.6, 0.6)], s, 0.05, 2)
+        out.append(sim.download().numpy())
+    assert np.array_equal(out[0], out[1])
