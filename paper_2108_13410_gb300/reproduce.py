@@ -99,6 +99,47 @@ def red_path_curvature(r: float, p: float = 0.5, dg: float = 1e-5, dt: float = 0
     return out
 
 
+def red_path_dos(r: float, g_points=(0.45, 0.35, 0.25, 0.15, 0.05), p: float = 0.5, dg: float = 1e-5,
+                 dt: float = 0.02, dtype: str = "c64", order: int = 2, renorm_every: int = 100):
+    """Density of states of Z~ = -sum_l sigma^z_l (Sec. V) along a broken red path.
+
+    psi_1 is carried O -> P(p, 0) -> R(p, r) and then along R -> R'(0, r); when g reaches
+    each value of g_points (descending) the histogram P(k) over the number k of links in
+    sigma^z = -1 (Z~ = 2k - n_links) is taken with qs_dos.  Returns the histograms, the
+    position of the largest bin and the number of maxima of each histogram (the paper
+    reads a single maximum in each phase for r < 0.16 as a second-order transition).
+    Reading of "maximum": in the deconfined phase the bins of even and odd k alternate
+    (the toric-code parity structure), so maxima are counted on the even-k and the odd-k
+    envelopes separately, each ignoring local maxima below 5% of its largest bin."""
+    import numpy as np
+    from . import Simulator, QS_OPT_RENORM_EVERY
+    from .protocol import prepare, segment
+    t0 = time.perf_counter()
+    sim = Simulator(3, 3, form="ug", dtype=dtype)
+    sim.set_option(QS_OPT_RENORM_EVERY, renorm_every)
+    sim.init_toric(0)
+    sim.evolve_path(prepare(p, dg, "g"), dt, order)
+    sim.evolve_path(segment((p, 0.0), (p, r), dg), dt, order)
+    g_now, out = p, []
+    for g in sorted(g_points, reverse=True):
+        if g < g_now:
+            sim.evolve_path(segment((g_now, r), (g, r), dg), dt, order)
+            g_now = g
+        h = sim.dos()[0]
+        maxima = []
+        for par in (0, 1):
+            v = h[par::2]
+            top = float(v.max())
+            maxima.append(sum(1 for i in range(len(v))
+                              if v[i] >= 0.05 * top and (i == 0 or v[i] > v[i - 1])
+                              and (i == len(v) - 1 or v[i] > v[i + 1])))
+        out.append({"g": g, "dos": h.tolist(), "maxima_even": maxima[0], "maxima_odd": maxima[1],
+                    "argmax_k": int(np.argmax(h)), "mean_k": float(np.dot(np.arange(len(h)), h)),
+                    "sum": float(h.sum())})
+    return {"r": r, "p": p, "dg": dg, "dt": dt, "dtype": dtype, "points": out,
+            "seconds": time.perf_counter() - t0}
+
+
 PRINTED_TABLE1 = {200: (0.03982, 4.79e-5), 500: (0.04009, 4.99e-5), 800: (0.04075, 4.98e-5)}
 
 

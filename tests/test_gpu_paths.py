@@ -123,3 +123,20 @@ def test_trotter_error_study_scales_as_second_order():
     assert d[10]["delta"] == 0.0
     assert 0.72 <= d[20]["delta"] / d[40]["delta"] <= 0.88
     assert 0.0 < d[40]["alpha"] < 1e-5
+
+
+@gpu
+def test_dos_along_red_paths():
+    """Density of states of Z~ along the broken red paths of Sec. V (complex64, dg = 1e-5):
+    the histograms are normalised; at r = 0.05 every histogram from g = 0.45 down to 0.04
+    has one maximum on each parity envelope (one maximum in each phase, the paper's
+    second-order reading), while at r = 0.25, past the meeting point of the critical
+    lines, the deconfined side has several."""
+    from paper_2108_13410_gb300.reproduce import red_path_dos
+    gs = (0.45, 0.30, 0.20, 0.12, 0.04)
+    low = red_path_dos(0.05, gs)
+    for pt in low["points"]:
+        assert abs(pt["sum"] - 1.0) <= 1e-5
+        assert pt["maxima_even"] == 1 and pt["maxima_odd"] == 1, pt
+    high = red_path_dos(0.25, gs)
+    assert max(pt["maxima_even"] + pt["maxima_odd"] for pt in high["points"]) > 2
