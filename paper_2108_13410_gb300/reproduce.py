@@ -54,6 +54,48 @@ def hysteresis(p: float, dg: float, dt: float, dtype: str = "c64", order: int = 
 PRINTED_CURVATURE_MIN = {0.05: 0.1920, 0.15: 0.1916, 0.25: 0.2489}
 
 
+def _curvature_minimum(g, e, k: int, h: float):
+    """(g, value) at the smallest central second difference of e over k samples (h in g),
+    evaluated at every sample and refined by a parabola through the smallest three."""
+    import numpy as np
+    d2 = (e[2 * k:] - 2 * e[k:-k] + e[:-2 * k]) / h ** 2          # at g[k:-k]
+    gd = g[k:-k]
+    i = int(np.argmin(d2[1:-1])) + 1
+    y0, y1, y2 = d2[i - 1], d2[i], d2[i + 1]
+    shift = 0.5 * (y0 - y2) / (y0 - 2 * y1 + y2)
+    return float(gd[i] + shift * (gd[i + 1] - gd[i])), float(y1 + 0.25 * (y0 - y2) * shift)
+
+
+PRINTED_DUAL_LINE_EXTREMUM = 0.1798
+
+
+def dual_line_curvature(p: float = 0.5, dg: float = 1e-5, dt: float = 0.02, every: int = 100,
+                        stencil: int = 10, dtype: str = "c64", order: int = 2, renorm_every: int = 100):
+    """Energy on the dual line g = lambda (Sec. V) and the extremum of its second derivative.
+
+    Reading of the path "from (0, p) through (p, p) to O": psi_1' is carried along the
+    lambda axis O -> (0, p) (the state of Sec. IV prepared at P'), then to (p, p), then along
+    g = lambda down to O with <H1(g, g)> measured every `every` steps; d^2E/dg^2 as in
+    red_path_curvature.  3x3 torus, unitary gauge, J = h = 1/2."""
+    import numpy as np
+    from . import Simulator, QS_OPT_RENORM_EVERY
+    from .protocol import prepare, segment, run_path
+    t0 = time.perf_counter()
+    sim = Simulator(3, 3, form="ug", dtype=dtype)
+    sim.set_option(QS_OPT_RENORM_EVERY, renorm_every)
+    sim.init_toric(1)
+    sim.evolve_path(prepare(p, dg, "lambda"), dt, order)
+    sim.evolve_path(segment((0.0, p), (p, p), dg), dt, order)
+    meas = run_path(sim, segment((p, p), (0.0, 0.0), dg), dt, order, measure_every=every)
+    g = np.array([c[0] for c, _ in meas])
+    e = np.array([v for _, v in meas])
+    h = stencil * every * dg
+    g_min, d2_min = _curvature_minimum(g, e, stencil, h)
+    return {"p": p, "dg": dg, "dt": dt, "dtype": dtype, "h": h, "points": len(g), "g_min": g_min,
+            "d2E_min": d2_min, "E_end": float(e[-1]), "printed_g_extremum": PRINTED_DUAL_LINE_EXTREMUM,
+            "steps": 3 * int(round(p / dg)), "seconds": time.perf_counter() - t0}
+
+
 def red_path_curvature(r: float, p: float = 0.5, dg: float = 1e-5, dt: float = 0.02, every: int = 100,
                        stencil: int = 10, dtype: str = "c64", order: int = 2, renorm_every: int = 100,
                        curve: bool = False):
@@ -79,16 +121,10 @@ def red_path_curvature(r: float, p: float = 0.5, dg: float = 1e-5, dt: float = 0
     meas = run_path(sim, segment((p, r), (0.0, r), dg), dt, order, measure_every=every)
     g = np.array([c[0] for c, _ in meas])
     e = np.array([v for _, v in meas])
-    k = stencil
-    h = k * every * dg
-    d2 = (e[2 * k:] - 2 * e[k:-k] + e[:-2 * k]) / h ** 2          # at g[k:-k]
-    gd = g[k:-k]
-    i = int(np.argmin(d2[1:-1])) + 1
-    y0, y1, y2 = d2[i - 1], d2[i], d2[i + 1]
-    shift = 0.5 * (y0 - y2) / (y0 - 2 * y1 + y2)
-    g_min = float(gd[i] + shift * (gd[i + 1] - gd[i]))
+    h = stencil * every * dg
+    g_min, d2_min = _curvature_minimum(g, e, stencil, h)
     out = {"r": r, "p": p, "dg": dg, "dt": dt, "dtype": dtype, "h": h, "points": len(g),
-           "g_min": g_min, "d2E_min": float(y1 + 0.25 * (y0 - y2) * shift),
+           "g_min": g_min, "d2E_min": d2_min,
            "E_end": float(e[-1]), "steps": int(round(p / dg)) + int(round(r / dg)) + int(round(p / dg)),
            "seconds": time.perf_counter() - t0}
     if r in PRINTED_CURVATURE_MIN:

@@ -140,3 +140,19 @@ def test_dos_along_red_paths():
         assert pt["maxima_even"] == 1 and pt["maxima_odd"] == 1, pt
     high = red_path_dos(0.25, gs)
     assert max(pt["maxima_even"] + pt["maxima_odd"] for pt in high["points"]) > 2
+
+
+@gpu
+def test_dual_line_curvature_extremum():
+    """The dual-line run of Sec. V (psi_1' carried to (0, 0.5), then to (0.5, 0.5), then
+    along lambda = g to O; dg = 1e-5, dt = 0.02, complex64 renormalised every 100 steps):
+    the minimum of d^2E/dg^2 lies within 0.005 of the oracle's ground-energy curvature
+    minimum (tests/golden/dual_line_curvature.txt) and of the printed g_3 = 0.1798."""
+    import os
+    from paper_2108_13410_gb300.reproduce import dual_line_curvature
+    path = os.path.join(os.path.dirname(__file__), "golden", "dual_line_curvature.txt")
+    (g_ed, _, printed), = [[float(x) for x in l.split()] for l in open(path)
+                           if l.strip() and not l.startswith("#")]
+    out = dual_line_curvature()
+    assert abs(out["g_min"] - g_ed) <= 0.005, (out["g_min"], g_ed)
+    assert abs(out["g_min"] - printed) <= 0.005, (out["g_min"], printed)
