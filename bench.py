@@ -55,11 +55,14 @@ def kernel_source_hash() -> str:
     return d.hexdigest()[:16]
 
 
-def profile_traffic(kernel_tag: str):
+def profile_traffic(kernel_tag: str, kernel_name: str = ""):
     """dram read+write bytes per launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+    taken on the current kernel source and on the same kernel instantiation (the
+    summary's first line starts with its name)."""
     path = os.path.join(ROOT, "profiles", f"{kernel_tag}.txt")
     if not os.path.exists(path):
+        return None
+    if kernel_name and not open(path).readline().startswith(kernel_name):
         return None
     h = kernel_source_hash()
     vals = {}
@@ -275,7 +278,7 @@ def run_ours(args):
     state_bytes = sim.state_bytes
     alg_bytes = 2.0 * state_bytes                     # one read + one write of the state per pass
     peak, peak_kind = peaks()
-    names = ("k_xpass_tma<3, true, false, true>", "k_xpass_tma<3, true, true, true>")
+    names = ("k_xpass_tma<3, true, false, true>", "k_xpass_tma<2, true, true, true>")
     tags = ("k_xpass_tma_c64_27q", "k_xpass_tma_shared_c64_27q")
     dom = 0 if kinds[0][0] >= kinds[1][0] else 1     # dominant kernel: larger total time
     per_kind = {}
@@ -289,7 +292,7 @@ def run_ours(args):
     avg_ms = kinds[dom][0] / max(1, kinds[dom][1])
     achieved = alg_bytes / (avg_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profile_traffic(tags[dom]),
+                "frac": achieved / peak, "traffic": profile_traffic(tags[dom], names[dom]),
                 "kernel": names[dom], "launches": kinds[dom][1], "avg_launch_ms": avg_ms,
                 "alg_bytes_per_launch": alg_bytes, "peak_kind": peak_kind,
                 "xpass_kernels": per_kind, "passes_per_step": xpass_n / K,

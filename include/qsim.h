@@ -105,11 +105,14 @@ typedef enum {
                                  one qubit group and one applies H, the Z layer and the
                                  next group's H, two passes fewer per step.  0: every
                                  factor group takes all its passes                    */
-    QS_OPT_PDL = 9            /* 1 (default): the TMA X passes are launched with
+    QS_OPT_PDL = 9,           /* 1 (default): the TMA X passes are launched with
                                  programmatic stream serialisation, so a pass is
                                  scheduled and sets up while the previous kernel
                                  drains and waits for its writes before reading
                                  global memory; 0: plain stream order             */
+    QS_OPT_SHARED_BUFFERS = 10 /* tile buffers per CTA of the shared X passes
+                                 (QS_OPT_XMERGE): 2 (default; three CTAs per SM) or 3
+                                 (two CTAs per SM)                                 */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open
@@ -220,13 +223,13 @@ int qs_num_links(const qs_sim *sim);
 qs_status qs_dos(qs_sim *sim, double *out);
 
 /* Autotuner: times n_steps second-order steps of every X-pass configuration that
- * applies (complex64: the persistent TMA kernel with 2 or 3 tile buffers and either
- * store mode, and the register-staged kernel; complex128: the register-staged kernel)
- * on the bound state, which is overwritten, and keeps the fastest (QS_OPT_XPASS,
- * QS_OPT_TMA_BUFFERS, QS_OPT_TMA_STORE).  Outputs the choice and its ms per step
- * (host). */
+ * applies (complex64: the persistent TMA kernel with 2 or 3 tile buffers for plain and
+ * for shared passes and either store mode, and the register-staged kernel; complex128:
+ * the register-staged kernel) on the bound state, which is overwritten, and keeps the
+ * fastest (QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_TMA_STORE, QS_OPT_SHARED_BUFFERS).
+ * Outputs the choice and its ms per step (host). */
 qs_status qs_autotune(qs_sim *sim, int n_steps, int *best_xpass, int *best_buffers, int *best_store,
-                      double *best_ms_per_step);
+                      int *best_shared_buffers, double *best_ms_per_step);
 
 /* Failure-detection self-test: launches a kernel that waits on an mbarrier which
  * never completes, with the same bounded wait as the TMA X pass, limited to

@@ -89,6 +89,7 @@ struct qs_sim {
     int tma_store = 1;                     // X pass writes tiles back with TMA stores
     int xmerge = 1;                        // share the pass of one qubit group between factor groups
     int pdl = 1;                           // X passes launched with programmatic stream serialisation
+    int nbuf_shared = 2;                   // TMA tile buffers of the shared passes (2 or 3)
     int tan_off = 0;                       // tangent triple in the operator record
     int nX0 = 0, nX1 = 0;                  // X qubits per class
     bool tan_active = false;               // this call's X passes use the tangent form
@@ -479,8 +480,9 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
         const bool tan = s->tan_active && (frame & 1);
         if (rec2 && (frame & 1) && !tan) FAIL(s, QS_ERR_STATE, "shared rotation pass needs the tangent form");
         P.xscale = tan ? xscale : 0;
-        size_t sm = tma_smem_bytes(s, s->nbuf, apply_z);
-        XpassTmaKernel kern = xpass_tma_kernel(s->nbuf, s->tma_store != 0, rec2 != nullptr, tan);
+        const int nb = rec2 ? s->nbuf_shared : s->nbuf;
+        size_t sm = tma_smem_bytes(s, nb, apply_z);
+        XpassTmaKernel kern = xpass_tma_kernel(nb, s->tma_store != 0, rec2 != nullptr, tan);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm);
         if (per_sm < 1) per_sm = 1;
@@ -931,7 +933,7 @@ qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_un
     const long long key[10] = {(long long)nops, order, n_steps, B, (long long)(uintptr_t)s->state[0],
                                (long long)(uintptr_t)s->d_rec, s->renorm_every,
                                s->xpass_impl * 16 + s->nbuf + 256 * s->tma_store + 1024 * s->xmerge +
-                                   4096 * (int)s->tan_active + 8192 * s->pdl,
+                                   4096 * (int)s->tan_active + 8192 * s->pdl + 16384 * s->nbuf_shared,
                                s->method, (long long)s->dtype};
     if (!s->graph_exec || memcmp(key, s->graph_key, sizeof(key)) != 0) {
         if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
@@ -1301,6 +1303,9 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
             s->xmerge = value != 0; return QS_OK;
         case QS_OPT_PDL:
             s->pdl = value != 0; return QS_OK;
+        case QS_OPT_SHARED_BUFFERS:
+            if (value != 2 && value != 3) FAIL(s, QS_ERR_ARG, "shared-pass TMA buffers must be 2 or 3");
+            s->nbuf_shared = (int)value; return QS_OK;
         case QS_OPT_ADJOINT:
             if (value < 0 || value > 3) FAIL(s, QS_ERR_ARG, "adjoint option must be 0..3");
             s->adj_impl = (value & 1) ? 1 : 0;
@@ -1715,17 +1720,19 @@ qs_status qs_dos(qs_sim *s, double *out) {
 }
 
 qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers, int *best_store,
-                      double *best_ms_per_step) {
+                      int *best_shared_buffers, double *best_ms_per_step) {
     qs_status st;
     if ((st = check_ready(s)) != QS_OK) return st;
     if (n_steps < 1 || n_steps > 1000) FAIL(s, QS_ERR_ARG, "n_steps must be in [1, 1000]");
-    if (!best_xpass || !best_buffers || !best_store || !best_ms_per_step) FAIL(s, QS_ERR_ARG, "null output");
-    struct Cand { int xpass, nbuf, store; };
+    if (!best_xpass || !best_buffers || !best_store || !best_shared_buffers || !best_ms_per_step)
+        FAIL(s, QS_ERR_ARG, "null output");
+    struct Cand { int xpass, nbuf, store, nsh; };
     std::vector<Cand> cands;
     if (s->dtype == QS_C64 && s->tmaps_ok)
         for (int nb = 2; nb <= 3; ++nb)
-            for (int so = 0; so <= 1; ++so) cands.push_back({2, nb, so});
-    cands.push_back({1, 2, 0});
+            for (int so = 0; so <= 1; ++so)
+                for (int ns = 2; ns <= 3; ++ns) cands.push_back({2, nb, so, ns});
+    cands.push_back({1, 2, 0, s->nbuf_shared});
     const int saved_method = s->method, saved_profile = s->profile, saved_graph = s->use_graph;
     s->method = 0; s->profile = 0; s->use_graph = 0;
     std::vector<qs_couplings> c(s->batch, qs_couplings{1.0, 1.0, 0.6, 0.6});
@@ -1737,7 +1744,7 @@ qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers
     double best = 1e300;
     Cand pick = cands.back();
     for (const Cand &cd : cands) {
-        s->xpass_impl = cd.xpass; s->nbuf = cd.nbuf; s->tma_store = cd.store;
+        s->xpass_impl = cd.xpass; s->nbuf = cd.nbuf; s->tma_store = cd.store; s->nbuf_shared = cd.nsh;
         if ((st = qs_init_plus(s)) != QS_OK) break;
         if ((st = qs_evolve(s, c.data(), sv.data(), 0.02, 2, 2)) != QS_OK) break;   // warm-up
         CK(s, cudaEventRecord(e0, s->stream));
@@ -1752,8 +1759,9 @@ qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers
     cudaEventDestroy(e1);
     s->method = saved_method; s->profile = saved_profile; s->use_graph = saved_graph;
     if (st != QS_OK) return st;
-    s->xpass_impl = pick.xpass; s->nbuf = pick.nbuf; s->tma_store = pick.store;
+    s->xpass_impl = pick.xpass; s->nbuf = pick.nbuf; s->tma_store = pick.store; s->nbuf_shared = pick.nsh;
     *best_xpass = pick.xpass; *best_buffers = pick.nbuf; *best_store = pick.store;
+    *best_shared_buffers = pick.nsh;
     *best_ms_per_step = best / n_steps;
     return QS_OK;
 }

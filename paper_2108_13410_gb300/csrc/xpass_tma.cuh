@@ -247,6 +247,25 @@ __device__ __forceinline__ void rotate_t(u64 (&w)[NR], unsigned mask, const int 
     }
 }
 
+// Tangent form with the constants of each register bit read from shared memory
+// (tc[k] = {(t, t), (-t, -t)} for the class of that bit), so no registers hold them
+// between stages and no selects pick them.
+__device__ __forceinline__ void rotate_ts(u64 (&w)[NR], unsigned mask, const u64 (*tc)[2]) {
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+        const u64 pt = tc[k][0], nt = tc[k][1];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (!((r >> k) & 1)) {
+                const int q = r | (1 << k);
+                const u64 a = w[r], b = w[q];
+                w[r] = fma2p(pt, b, a);
+                w[q] = fma2p(nt, a, b);
+            }
+    }
+}
+
 __device__ __forceinline__ void rot_apply(u64 (&w)[NR], unsigned mask, const int (&cls)[RB], const RotConst &C) {
     rotate_w(w, mask, cls, C);
 }
@@ -315,6 +334,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
     __shared__ int s_ok;
     typedef typename std::conditional<TAN, TanConst, RotConst>::type XC;
     __shared__ XC s_rc2;           // MERGED: rotation constants of the second round
+    __shared__ u64 s_tc[2][3][RB][2];   // TAN: per round, stage and register bit: (t,t), (-t,-t)
 
     const int t = threadIdx.x;
     const long long G = gridDim.x;
@@ -412,14 +432,24 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             // operator record of this batch element (angles, phase table)
             __syncthreads();
             const double *rec = recs + batch * rec_stride;
-            load_xconst(RC, rec, P.tan_off);
-            if (TAN) xs = (float)rec[P.tan_off + 2];
+            if (TAN) {
+                xs = (float)rec[P.tan_off + 2];
+                if (t < (MERGED ? 2 : 1) * 3 * RB) {
+                    const int round = t / (3 * RB), st = (t / RB) % 3, k = t % RB;
+                    const double *rr = round ? recs2 + batch * rec_stride : rec;
+                    const float tv = (float)rr[P.tan_off + ((P.cls[st] >> k) & 1)];
+                    s_tc[round][st][k][0] = pk(tv, tv);
+                    s_tc[round][st][k][1] = pk(-tv, -tv);
+                }
+            } else {
+                load_xconst(RC, rec, P.tan_off);
+            }
             if (P.apply_z) {
                 const int loff = TAN ? P.tan_off + 4 : P.lut_off;   // tangent form: table scaled by C
                 for (int i = t; i < nlut; i += NT)
                     lut[i] = make_float2((float)rec[loff + 2 * i], (float)rec[loff + 2 * i + 1]);
             }
-            if (MERGED && t == 0) load_xconst(s_rc2, recs2 + batch * rec_stride, P.tan_off);
+            if (!TAN && MERGED && t == 0) load_xconst(s_rc2, recs2 + batch * rec_stride, P.tan_off);
             cur_batch = batch;
         }
         if (t == 0) {
@@ -450,7 +480,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                 w[r] = pk(v.x, v.y);
             }
         }
-        if (P.frame & 1) rot_apply(w, P.rot[0], cls0, RC);
+        if (P.frame & 1) { if (TAN) rotate_ts(w, P.rot[0], s_tc[0][0]); else rot_apply(w, P.rot[0], cls0, RC); }
         else hadamard_w(w, P.rot[0]);
 #pragma unroll
         for (int r = 0; r < NR; ++r) tb[a_base + (r << TB)] = w[r];
@@ -464,7 +494,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                 w[2 * m] = q.x;
                 w[2 * m + 1] = q.y;
             }
-            if (P.frame & 1) rot_apply(w, P.rot[1], cls1, RC);
+            if (P.frame & 1) { if (TAN) rotate_ts(w, P.rot[1], s_tc[0][1]); else rot_apply(w, P.rot[1], cls1, RC); }
             else hadamard_w(w, P.rot[1]);
 #pragma unroll
             for (int m = 0; m < NR / 2; ++m) tb2[b_base + (m ^ b_x)] = make_ulonglong2(w[2 * m], w[2 * m + 1]);
@@ -473,7 +503,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         // ---- stage C: registers = local 4..7; diagonal phase; store ----
 #pragma unroll
         for (int r = 0; r < NR; ++r) w[r] = tb[c_base[r & 7] + (r << 4)];
-        if (P.frame & 1) rot_apply(w, P.rot[2], cls2, RC);
+        if (P.frame & 1) { if (TAN) rotate_ts(w, P.rot[2], s_tc[0][2]); else rot_apply(w, P.rot[2], cls2, RC); }
         else hadamard_w(w, P.rot[2]);
         // global base of the tile: mid bits -> global c.., upper bits (and batch) -> next+k..
         const long long mid = tile & ((1ll << P.mid_bits) - 1);
@@ -513,8 +543,12 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         if (MERGED) {
             // ---- second round: stage C (still in registers), B, A; store from A ----
             if (P.frame & 1) {
-                const XC R2 = s_rc2;
-                rot_apply(w, P.rot[2], cls2, R2);
+                if (TAN) {
+                    rotate_ts(w, P.rot[2], s_tc[1][2]);
+                } else {
+                    const XC R2 = s_rc2;
+                    rot_apply(w, P.rot[2], cls2, R2);
+                }
             } else {
                 hadamard_w(w, P.rot[2]);
             }
@@ -530,8 +564,12 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                     w[2 * m + 1] = q.y;
                 }
                 if (P.frame & 1) {
-                    const XC R2 = s_rc2;
-                    rot_apply(w, P.rot[1], cls1, R2);
+                    if (TAN) {
+                        rotate_ts(w, P.rot[1], s_tc[1][1]);
+                    } else {
+                        const XC R2 = s_rc2;
+                        rot_apply(w, P.rot[1], cls1, R2);
+                    }
                 } else {
                     hadamard_w(w, P.rot[1]);
                 }
@@ -542,8 +580,12 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
 #pragma unroll
             for (int r = 0; r < NR; ++r) w[r] = tb[a_base + (r << TB)];
             if (P.frame & 1) {
-                const XC R2 = s_rc2;
-                rot_apply(w, P.rot[0], cls0, R2);
+                if (TAN) {
+                    rotate_ts(w, P.rot[0], s_tc[1][0]);
+                } else {
+                    const XC R2 = s_rc2;
+                    rot_apply(w, P.rot[0], cls0, R2);
+                }
             } else {
                 hadamard_w(w, P.rot[0]);
             }

@@ -23,7 +23,7 @@ QS_GAUGE_HIGGS, QS_UNITARY_GAUGE = 0, 1
 QS_C64, QS_C128 = 0, 1
 QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
 QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_ADJOINT, \
-    QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL = range(10)
+    QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL, QS_OPT_SHARED_BUFFERS = range(11)
 
 
 class QsError(RuntimeError):
@@ -70,7 +70,7 @@ _SIGS = {
     "qs_selftest_wait": ([_P, _D], _I),
     "qs_num_links": ([_P], _I),
     "qs_dos": ([_P, _DP], _I),
-    "qs_autotune": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _DP], _I),
+    "qs_autotune": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _DP], _I),
     "qs_save": ([_P, ctypes.c_char_p], _I),
     "qs_load": ([_P, ctypes.c_char_p], _I),
     "qs_scan": ([_P, _CP, _I, _DP, _D, _I, _I, _DP], _I),
@@ -277,12 +277,12 @@ def qs_dos(sim, batch: int = 1):
 
 
 def qs_autotune(sim, n_steps: int = 20):
-    """Returns (xpass kernel, tile buffers, store mode, ms per step) of the fastest
-    configuration."""
-    xp, nb, so, ms = _I(), _I(), _I(), ctypes.c_double()
+    """Returns (xpass kernel, tile buffers, store mode, shared-pass tile buffers, ms per
+    step) of the fastest configuration."""
+    xp, nb, so, ns, ms = _I(), _I(), _I(), _I(), ctypes.c_double()
     _check(sim, library().qs_autotune(sim, n_steps, ctypes.byref(xp), ctypes.byref(nb), ctypes.byref(so),
-                                      ctypes.byref(ms)))
-    return xp.value, nb.value, so.value, ms.value
+                                      ctypes.byref(ns), ctypes.byref(ms)))
+    return xp.value, nb.value, so.value, ns.value, ms.value
 
 
 def qs_selftest_wait(sim, limit_ms: float):
@@ -443,14 +443,15 @@ class Simulator:
                 table = json.load(open(path))
             except (OSError, ValueError):
                 table = {}
-        if cache and key in table and "store" in table[key]:
-            xp, nb, so = table[key]["xpass"], table[key]["buffers"], table[key]["store"]
-            self.set_option(QS_OPT_XPASS, xp)
-            self.set_option(QS_OPT_TMA_BUFFERS, nb)
-            self.set_option(QS_OPT_TMA_STORE, so)
-            return table[key]
-        xp, nb, so, ms = qs_autotune(self.h, n_steps)
-        entry = {"xpass": xp, "buffers": nb, "store": so, "ms_per_step": ms}
+        if cache and key in table and "shared_buffers" in table[key]:
+            e = table[key]
+            self.set_option(QS_OPT_XPASS, e["xpass"])
+            self.set_option(QS_OPT_TMA_BUFFERS, e["buffers"])
+            self.set_option(QS_OPT_TMA_STORE, e["store"])
+            self.set_option(QS_OPT_SHARED_BUFFERS, e["shared_buffers"])
+            return e
+        xp, nb, so, ns, ms = qs_autotune(self.h, n_steps)
+        entry = {"xpass": xp, "buffers": nb, "store": so, "shared_buffers": ns, "ms_per_step": ms}
         if cache:
             table[key] = entry
             try:

@@ -51,15 +51,19 @@ def test_two_pass_lattice_matches_oracle(order, n_steps, store):
 
 @gpu
 @pytest.mark.parametrize("order,n_steps", [(2, 1), (2, 4), (1, 3)])
-def test_three_pass_lattice_matches_oracle(order, n_steps):
+@pytest.mark.parametrize("nsh", [2, 3])
+def test_three_pass_lattice_matches_oracle(order, n_steps, nsh):
     """2x4 torus, gauge-Higgs form: 24 qubits, three passes per X layer (qubits
     0-11, 12-19, 20-23): the shared pass alternates between the second and the third
-    qubit group, the first runs alone in the middle of every factor group."""
+    qubit group, the first runs alone in the middle of every factor group.  Shared
+    passes with 2 or 3 tile buffers (QS_OPT_SHARED_BUFFERS)."""
+    from paper_2108_13410_gb300.qsim import QS_OPT_SHARED_BUFFERS
     lat = OracleLattice(2, 4, True, "gh")
     c = Couplings(0.7, 0.4)
     T = 0.15 * n_steps
     s = O.schedule_linear(T, n_steps)
     sim = _sim(2, 4, form="gh", dtype="c64")
+    sim.set_option(QS_OPT_SHARED_BUFFERS, nsh)
     sim.init_plus()
     sim.evolve([(0.7, 0.4)], s, T / n_steps, order)
     _assert_amplitudes(sim.download()[0].numpy(), O.evolve(lat, c, s, T / n_steps, order))
