@@ -334,7 +334,8 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
     __shared__ int s_ok;
     typedef typename std::conditional<TAN, TanConst, RotConst>::type XC;
     __shared__ XC s_rc2;           // MERGED: rotation constants of the second round
-    __shared__ u64 s_tc[2][3][RB][2];   // TAN: per round, stage and register bit: (t,t), (-t,-t)
+    __shared__ u64 s_tc[2][3][RB][2];   // TAN and MERGED: per round, stage and register bit:
+                                        // (t,t), (-t,-t); plain passes keep them in registers
 
     const int t = threadIdx.x;
     const long long G = gridDim.x;
@@ -432,9 +433,10 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
             // operator record of this batch element (angles, phase table)
             __syncthreads();
             const double *rec = recs + batch * rec_stride;
+            if (TAN && !MERGED) load_xconst(RC, rec, P.tan_off);
             if (TAN) {
                 xs = (float)rec[P.tan_off + 2];
-                if (t < (MERGED ? 2 : 1) * 3 * RB) {
+                if (MERGED && t < 2 * 3 * RB) {
                     const int round = t / (3 * RB), st = (t / RB) % 3, k = t % RB;
                     const double *rr = round ? recs2 + batch * rec_stride : rec;
                     const float tv = (float)rr[P.tan_off + ((P.cls[st] >> k) & 1)];
@@ -480,7 +482,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                 w[r] = pk(v.x, v.y);
             }
         }
-        if (P.frame & 1) { if (TAN) rotate_ts(w, P.rot[0], s_tc[0][0]); else rot_apply(w, P.rot[0], cls0, RC); }
+        if (P.frame & 1) { if (TAN && MERGED) rotate_ts(w, P.rot[0], s_tc[0][0]); else rot_apply(w, P.rot[0], cls0, RC); }
         else hadamard_w(w, P.rot[0]);
 #pragma unroll
         for (int r = 0; r < NR; ++r) tb[a_base + (r << TB)] = w[r];
@@ -494,7 +496,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
                 w[2 * m] = q.x;
                 w[2 * m + 1] = q.y;
             }
-            if (P.frame & 1) { if (TAN) rotate_ts(w, P.rot[1], s_tc[0][1]); else rot_apply(w, P.rot[1], cls1, RC); }
+            if (P.frame & 1) { if (TAN && MERGED) rotate_ts(w, P.rot[1], s_tc[0][1]); else rot_apply(w, P.rot[1], cls1, RC); }
             else hadamard_w(w, P.rot[1]);
 #pragma unroll
             for (int m = 0; m < NR / 2; ++m) tb2[b_base + (m ^ b_x)] = make_ulonglong2(w[2 * m], w[2 * m + 1]);
@@ -503,7 +505,7 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
         // ---- stage C: registers = local 4..7; diagonal phase; store ----
 #pragma unroll
         for (int r = 0; r < NR; ++r) w[r] = tb[c_base[r & 7] + (r << 4)];
-        if (P.frame & 1) { if (TAN) rotate_ts(w, P.rot[2], s_tc[0][2]); else rot_apply(w, P.rot[2], cls2, RC); }
+        if (P.frame & 1) { if (TAN && MERGED) rotate_ts(w, P.rot[2], s_tc[0][2]); else rot_apply(w, P.rot[2], cls2, RC); }
         else hadamard_w(w, P.rot[2]);
         // global base of the tile: mid bits -> global c.., upper bits (and batch) -> next+k..
         const long long mid = tile & ((1ll << P.mid_bits) - 1);
