@@ -111,8 +111,10 @@ typedef enum {
                                  drains and waits for its writes before reading
                                  global memory; 0: plain stream order             */
     QS_OPT_SHARED_BUFFERS = 10 /* tile buffers per CTA of the shared X passes
-                                 (QS_OPT_XMERGE): 2 (default; three CTAs per SM) or 3
-                                 (two CTAs per SM)                                 */
+                                 (QS_OPT_XMERGE): 2 (three CTAs per SM), 3 (two CTAs
+                                 per SM) or 0 (default): 2 for tangent-form rotations
+                                 (gauge-Higgs), 3 for Walsh-Hadamard passes (unitary
+                                 gauge), the faster of the two for each as measured */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open

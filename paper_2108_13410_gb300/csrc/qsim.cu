@@ -89,7 +89,7 @@ struct qs_sim {
     int tma_store = 1;                     // X pass writes tiles back with TMA stores
     int xmerge = 1;                        // share the pass of one qubit group between factor groups
     int pdl = 1;                           // X passes launched with programmatic stream serialisation
-    int nbuf_shared = 2;                   // TMA tile buffers of the shared passes (2 or 3)
+    int nbuf_shared = 0;                   // TMA tile buffers of the shared passes (0 auto, 2 or 3)
     int tan_off = 0;                       // tangent triple in the operator record
     int nX0 = 0, nX1 = 0;                  // X qubits per class
     bool tan_active = false;               // this call's X passes use the tangent form
@@ -480,7 +480,9 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
         const bool tan = s->tan_active && (frame & 1);
         if (rec2 && (frame & 1) && !tan) FAIL(s, QS_ERR_STATE, "shared rotation pass needs the tangent form");
         P.xscale = tan ? xscale : 0;
-        const int nb = rec2 ? s->nbuf_shared : s->nbuf;
+        // shared passes: 0 = by form (tangent rotations fit three CTAs per SM with two
+        // buffers; the Walsh-Hadamard ones measured faster with three buffers)
+        const int nb = rec2 ? (s->nbuf_shared ? s->nbuf_shared : (tan ? 2 : 3)) : s->nbuf;
         size_t sm = tma_smem_bytes(s, nb, apply_z);
         XpassTmaKernel kern = xpass_tma_kernel(nb, s->tma_store != 0, rec2 != nullptr, tan);
         int per_sm = 0;
@@ -1304,7 +1306,8 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
         case QS_OPT_PDL:
             s->pdl = value != 0; return QS_OK;
         case QS_OPT_SHARED_BUFFERS:
-            if (value != 2 && value != 3) FAIL(s, QS_ERR_ARG, "shared-pass TMA buffers must be 2 or 3");
+            if (value != 0 && value != 2 && value != 3)
+                FAIL(s, QS_ERR_ARG, "shared-pass TMA buffers must be 0 (by form), 2 or 3");
             s->nbuf_shared = (int)value; return QS_OK;
         case QS_OPT_ADJOINT:
             if (value < 0 || value > 3) FAIL(s, QS_ERR_ARG, "adjoint option must be 0..3");
@@ -1732,7 +1735,7 @@ qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers
         for (int nb = 2; nb <= 3; ++nb)
             for (int so = 0; so <= 1; ++so)
                 for (int ns = 2; ns <= 3; ++ns) cands.push_back({2, nb, so, ns});
-    cands.push_back({1, 2, 0, s->nbuf_shared});
+    cands.push_back({1, 2, 0, 0});
     const int saved_method = s->method, saved_profile = s->profile, saved_graph = s->use_graph;
     s->method = 0; s->profile = 0; s->use_graph = 0;
     std::vector<qs_couplings> c(s->batch, qs_couplings{1.0, 1.0, 0.6, 0.6});

@@ -146,7 +146,7 @@ def test_autotune_picks_a_valid_configuration(tmp_path, monkeypatch):
     sim = _sim(3, 3, form="gh", dtype="c64")
     e = sim.autotune(n_steps=4)
     assert e["xpass"] in (1, 2) and e["buffers"] in (2, 3) and e["store"] in (0, 1) and e["ms_per_step"] > 0
-    assert e["shared_buffers"] in (2, 3)
+    assert e["shared_buffers"] in (0, 2, 3)          # 0: chosen by form
     again = sim.autotune(n_steps=4)           # from the cache
     keys = ("xpass", "buffers", "store", "shared_buffers")
     assert [again[k] for k in keys] == [e[k] for k in keys]
