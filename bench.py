@@ -46,6 +46,16 @@ def peaks():
     return 6800.0, "fallback"
 
 
+def workload_config(world: int) -> dict:
+    """The bench workload's `config` (the same for both arms)."""
+    W = WORKLOAD
+    return {"workload": W["name"], "lattice": "3x3 periodic", "form": "gauge-Higgs", "qubits": 27,
+            "g": W["g"], "lambda": W["lam"], "J": 1.0, "h": 1.0, "T": W["T"], "dt": W["T"] / W["total_steps"],
+            "order": W["order"], "state_bytes": 8 << 27,
+            "l2": "inputs larger than L2 (1.07 GB state, 129 MB L2)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def kernel_source_hash() -> str:
     """sha256 (16 hex digits) of the X-pass kernel sources."""
     import hashlib
@@ -221,7 +231,7 @@ def run_reference(args):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD["name"], "qubits": 27},
+           "config": workload_config(1),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": f"each step: {descs[-1]}"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -361,11 +371,7 @@ def run_ours(args):
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
                "warmup": Wu, "ms_per_step": ms_max / K, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-               "config": {"workload": W["name"], "lattice": "3x3 periodic", "form": "gauge-Higgs",
-                          "qubits": 27, "g": W["g"], "lambda": W["lam"], "J": 1.0, "h": 1.0,
-                          "T": W["T"], "dt": dt, "order": W["order"], "state_bytes": state_bytes,
-                          "l2": "inputs larger than L2 (1.07 GB state, 129 MB L2)",
-                          "parallelism": "replicas" if world > 1 else "single"},
+               "config": workload_config(world),
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                "clocks": clk}
         out.update(extra)
