@@ -92,11 +92,18 @@ __device__ __forceinline__ void adj_rotate(u64 (&p)[NR], u64 (&l)[NR], unsigned 
     adj_rotate_t(p, l, mask, cls, C, corr, qi0, qi1, g0, g1);
 }
 
-template <int NBUF, bool TAN>
+// MERGED (tangent form only): a shared reverse pass over one qubit group G.  Round 1
+// un-rotates X(G) of factor group j (terms to partials at slot0), then the Z layer of
+// group j-1 is undone in the stage-C layout (its terms and its scaled table, recs2), and
+// round 2 un-rotates X(G) of group j-1 in stages C, B, A (terms to partials2 at slot0b)
+// and stores from the stage-A layout.  Mirrors the shared passes of the forward sweep.
+template <int NBUF, bool TAN, bool MERGED>
 __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__restrict__ psi, float2 *__restrict__ lam,
                                                    const double *__restrict__ recs, int rec_stride, int tiles_shift,
                                                    int *__restrict__ err_flag, double *__restrict__ partials,
                                                    int nblk, int slot0, int zinv,
+                                                   const double *__restrict__ recs2,
+                                                   double *__restrict__ partials2, int slot0b,
                                                    const __grid_constant__ CUtensorMap tmap_p,
                                                    const __grid_constant__ CUtensorMap tmap_l,
                                                    const __grid_constant__ TmaPass P) {
@@ -108,7 +115,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
     uint2 *ptab = reinterpret_cast<uint2 *>(lut + (P.nA + 1) * (P.nB + 1));  // 3 x 256
     __shared__ uint64_t bars[NBUF];
     __shared__ int s_ok;
-    __shared__ double red[NT / 32][4];
+    __shared__ double red[NT / 32][8];
 
     const int t = threadIdx.x;
     const long long G = gridDim.x;
@@ -163,6 +170,18 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
     for (int j = 0; j < 8; ++j)
         if ((t >> j) & 1) { paA_t ^= P.paA_thr[j]; pbA_t ^= P.pbA_thr[j]; }
     const int nB1 = P.nB + 1, nlut = (P.nA + 1) * nB1;
+    uint32_t paC_t = 0, pbC_t = 0;                   // MERGED: stage-C thread parity columns
+    long long toff_a = 0;                            // MERGED: stage-A store offset
+    if (MERGED) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if ((tlo >> j) & 1) { paC_t ^= P.pa_thr[j]; pbC_t ^= P.pb_thr[j]; }
+            if ((thi >> j) & 1) { paC_t ^= P.pa_thr[4 + j]; pbC_t ^= P.pb_thr[4 + j]; }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if ((t >> j) & 1) toff_a += P.toff_a[j];
+    }
     int cls0[RB], cls1[RB], cls2[RB];
 #pragma unroll
     for (int kk = 0; kk < RB; ++kk) {
@@ -175,7 +194,27 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
     float corr[3] = {1.f, 1.f, 1.f};
     float qi0 = 1.f, qi1 = 1.f;     // 1 / (1 + t^2) per class
     float xs = 1.f;
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    XC RC2;                          // MERGED: the previous factor group's constants
+    float corr2[3] = {1.f, 1.f, 1.f};
+    float qj0 = 1.f, qj1 = 1.f;
+    constexpr int NV = MERGED ? 8 : 4;
+    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    // block sums of one batch element: values 0..3 to partials, 4..7 (MERGED) to partials2
+    auto flush = [&](long long bat) {
+        __syncthreads();
+        for (int v = 0; v < NV; ++v) {
+            double x = warp_sum(acc[v]);
+            if ((t & 31) == 0) red[t >> 5][v] = x;
+        }
+        __syncthreads();
+        if (t < NV) {
+            double sum = 0.0;
+            for (int w = 0; w < NT / 32; ++w) sum += red[w][t];
+            if (t < 4) partials[(bat * nblk + slot0 + blockIdx.x) * RED_NV + t] = sum;
+            else partials2[(bat * nblk + slot0b + blockIdx.x) * RED_NV + (t - 4)] = sum;
+        }
+        for (int v = 0; v < 8; ++v) acc[v] = 0.0;
+    };
 
     long long tile = first;
     for (int it = 0; it < n_my; ++it, tile += G) {
@@ -183,21 +222,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
         const uint32_t parity = (uint32_t)((it / NBUF) & 1);
         const long long batch = tile >> tiles_shift;
         if (batch != cur_batch) {
-            if (cur_batch >= 0) {
-                // flush the previous batch element's sums
-                __syncthreads();
-                for (int v = 0; v < 4; ++v) {
-                    double x = warp_sum(acc[v]);
-                    if ((t & 31) == 0) red[t >> 5][v] = x;
-                }
-                __syncthreads();
-                if (t < 4) {
-                    double sum = 0.0;
-                    for (int w = 0; w < NT / 32; ++w) sum += red[w][t];
-                    partials[(cur_batch * nblk + slot0 + blockIdx.x) * RED_NV + t] = sum;
-                }
-                acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
-            }
+            if (cur_batch >= 0) flush(cur_batch);   // the previous batch element's sums
             __syncthreads();
             const double *rec = recs + batch * rec_stride;
             load_xconst(RC, rec, P.tan_off);
@@ -214,6 +239,18 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
                 const int loff = TAN ? P.tan_off + 4 : 4;
                 for (int i = t; i < nlut; i += NT)
                     lut[i] = make_float2((float)rec[loff + 2 * i], -(float)rec[loff + 2 * i + 1]);
+            }
+            if (MERGED) {   // the previous factor group: constants, scale corrections, Z table
+                const double *rec2 = recs2 + batch * rec_stride;
+                load_xconst(RC2, rec2, P.tan_off);
+                const double q0 = 1.0 + rec2[P.tan_off] * rec2[P.tan_off];
+                const double q1 = 1.0 + rec2[P.tan_off + 1] * rec2[P.tan_off + 1];
+                for (int st = 0; st < 3; ++st)
+                    corr2[st] = (float)(pow(q0, (double)P.adj_u2[st][0]) * pow(q1, (double)P.adj_u2[st][1]));
+                qj0 = (float)(1.0 / q0);
+                qj1 = (float)(1.0 / q1);
+                for (int i = t; i < nlut; i += NT)
+                    lut[i] = make_float2((float)rec2[P.tan_off + 4 + 2 * i], -(float)rec2[P.tan_off + 5 + 2 * i]);
             }
             cur_batch = batch;
         }
@@ -311,25 +348,65 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
         }
         const long long mid = tile & ((1ll << P.mid_bits) - 1);
         const long long up = tile >> P.mid_bits;
-        const long long gbase = (mid << P.c) + (up << (P.next + P.k)) + toff;
-        u64 *dp = reinterpret_cast<u64 *>(psi + gbase);
-        u64 *dl = reinterpret_cast<u64 *>(lam + gbase);
+        if (MERGED) {
+            // ---- the previous factor group's Z layer, undone in the stage-C layout ----
+            float g0b = 0.f, g1b = 0.f, ga2 = 0.f, gb2 = 0.f;
+            {
+                const uint2 e0 = ptab[tin & 255], e1 = ptab[256 + ((tin >> 8) & 255)], e2 = ptab[512 + ((tin >> 16) & 255)];
+                const uint32_t pa = paC_t ^ e0.x ^ e1.x ^ e2.x, pb = pbC_t ^ e0.y ^ e1.y ^ e2.y;
 #pragma unroll
-        for (int r = 0; r < NR; ++r) { dp[P.roff_c[r]] = p[r]; dl[P.roff_c[r]] = l[r]; }
-        acc[0] += (double)g0; acc[1] += (double)g1; acc[2] += (double)ga; acc[3] += (double)gb;
+                for (int r = 0; r < NR; ++r) {
+                    const int oa = __popc(pa ^ P.pa_reg[r]), ob = __popc(pb ^ P.pb_reg[r]);
+                    const float im = idot(l[r], p[r]);
+                    ga2 += im * (float)(P.nA - 2 * oa);
+                    gb2 += im * (float)(P.nB - 2 * ob);
+                    const float2 ph = lut[oa * nB1 + ob];
+                    const float2 vp = cphase(unpk(p[r]), ph), vl = cphase(unpk(l[r]), ph);
+                    p[r] = pk(vp.x, vp.y);
+                    l[r] = pk(vl.x, vl.y);
+                }
+            }
+            // ---- round 2: the previous factor group's X on the same qubits, stages C, B, A ----
+            adj_rotate(p, l, P.rot[2], cls2, RC2, corr2[2], qj0, qj1, g0b, g1b);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) { tp[c_base[r & 7] + (r << 4)] = p[r]; tl[c_base[r & 7] + (r << 4)] = l[r]; }
+            __syncthreads();
+            if (P.stage_b) {
+                ulonglong2 *tp2 = reinterpret_cast<ulonglong2 *>(tp), *tl2 = reinterpret_cast<ulonglong2 *>(tl);
+#pragma unroll
+                for (int m = 0; m < NR / 2; ++m) {
+                    const ulonglong2 qp = tp2[b_base + (m ^ b_x)], ql = tl2[b_base + (m ^ b_x)];
+                    p[2 * m] = qp.x; p[2 * m + 1] = qp.y;
+                    l[2 * m] = ql.x; l[2 * m + 1] = ql.y;
+                }
+                adj_rotate(p, l, P.rot[1], cls1, RC2, corr2[1], qj0, qj1, g0b, g1b);
+#pragma unroll
+                for (int m = 0; m < NR / 2; ++m) {
+                    tp2[b_base + (m ^ b_x)] = make_ulonglong2(p[2 * m], p[2 * m + 1]);
+                    tl2[b_base + (m ^ b_x)] = make_ulonglong2(l[2 * m], l[2 * m + 1]);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int r = 0; r < NR; ++r) { p[r] = tp[a_base + (r << TB)]; l[r] = tl[a_base + (r << TB)]; }
+            adj_rotate(p, l, P.rot[0], cls0, RC2, corr2[0], qj0, qj1, g0b, g1b);
+            const long long gbase = (mid << P.c) + (up << (P.next + P.k)) + toff_a;
+            u64 *dp = reinterpret_cast<u64 *>(psi + gbase);
+            u64 *dl = reinterpret_cast<u64 *>(lam + gbase);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) { dp[P.roff_a[r]] = p[r]; dl[P.roff_a[r]] = l[r]; }
+            acc[0] += (double)g0; acc[1] += (double)g1;
+            acc[4] += (double)g0b; acc[5] += (double)g1b; acc[6] += (double)ga2; acc[7] += (double)gb2;
+        } else {
+            const long long gbase = (mid << P.c) + (up << (P.next + P.k)) + toff;
+            u64 *dp = reinterpret_cast<u64 *>(psi + gbase);
+            u64 *dl = reinterpret_cast<u64 *>(lam + gbase);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) { dp[P.roff_c[r]] = p[r]; dl[P.roff_c[r]] = l[r]; }
+            acc[0] += (double)g0; acc[1] += (double)g1; acc[2] += (double)ga; acc[3] += (double)gb;
+        }
     }
-    // flush the last batch element's sums
-    __syncthreads();
-    for (int v = 0; v < 4; ++v) {
-        double x = warp_sum(acc[v]);
-        if ((t & 31) == 0) red[t >> 5][v] = x;
-    }
-    __syncthreads();
-    if (t < 4 && cur_batch >= 0) {
-        double sum = 0.0;
-        for (int w = 0; w < NT / 32; ++w) sum += red[w][t];
-        partials[(cur_batch * nblk + slot0 + blockIdx.x) * RED_NV + t] = sum;
-    }
+    if (cur_batch >= 0) flush(cur_batch);   // the last batch element's sums
 }
 
 }  // namespace qsim

@@ -443,12 +443,14 @@ XpassTmaKernel xpass_tma_kernel(int nbuf, bool store_tma, bool merged, bool tan)
 }
 
 typedef void (*AdjKernel)(float2 *, float2 *, const double *, int, int, int *, double *, int, int, int,
-                          const CUtensorMap, const CUtensorMap, const TmaPass);
+                          const double *, double *, int, const CUtensorMap, const CUtensorMap, const TmaPass);
 
-// k_adj_tma instantiation for (tile buffers, tangent form)
-AdjKernel adj_tma_kernel(int nbuf, bool tan) {
-    if (nbuf == 1) return tan ? k_adj_tma<1, true> : k_adj_tma<1, false>;
-    return tan ? k_adj_tma<2, true> : k_adj_tma<2, false>;
+// k_adj_tma instantiation for (tile buffers, tangent form, shared reverse pass); shared
+// reverse passes exist in the tangent form only
+AdjKernel adj_tma_kernel(int nbuf, bool tan, bool merged = false) {
+    if (nbuf == 1) return tan ? (merged ? k_adj_tma<1, true, true> : k_adj_tma<1, true, false>)
+                              : k_adj_tma<1, false, false>;
+    return tan ? (merged ? k_adj_tma<2, true, true> : k_adj_tma<2, true, false>) : k_adj_tma<2, false, false>;
 }
 
 // One X pass.  rec2 != nullptr selects the merged TMA pass: X of the pass's qubits from
@@ -1032,8 +1034,22 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
         Gt = (unsigned)std::min<long long>((long long)B << (s->n - LT), (long long)per_sm * s->sm_count);
     }
     const size_t nblk_t = (size_t)np * Gt;
-    if ((st = grow(s, &s->d_adj_part, &s->adj_part_cap, std::max(nblk, nblk_t) * B * RED_NV, false)) != QS_OK)
+    // TMA path: one partial-sum region per factor group, two used in turn (a shared reverse
+    // pass writes the terms of two consecutive groups)
+    const size_t region = nblk_t * B * RED_NV;
+    if ((st = grow(s, &s->d_adj_part, &s->adj_part_cap, std::max(nblk * B * RED_NV, 2 * region), false)) != QS_OK)
         return st;
+    // shared reverse passes: consecutive factor groups meet on one qubit group, as in the
+    // forward sweep (orders ga, 0 .. np-3, gb and gb, 0 .. np-3, ga; ga = np-2, gb = np-1)
+    const bool share = adj_tan && s->xmerge && np >= 2;
+    const AdjKernel adj_kern_m = adj_tma_kernel(s->adj_nbuf, true, true);
+    int ord[2][64];
+    for (int i = 0; i < np; ++i) {
+        ord[0][i] = i == 0 ? np - 2 : (i == np - 1 ? np - 1 : i - 1);
+        ord[1][i] = i == 0 ? np - 1 : (i == np - 1 ? np - 2 : i - 1);
+    }
+    bool carried = false;   // the first qubit group of op jj was un-rotated by op jj+1's last pass
+    int dir = 0, carry_done[2] = {0, 0};
     if ((st = grow(s, &s->d_grad, &s->grad_cap, nops * B * RED_NV, false)) != QS_OK) return st;
     if ((st = grow(s, &s->h_grad, &s->h_grad_cap, nops * B * RED_NV, true)) != QS_OK) return st;
     size_t chunk0 = (size_t)-1;   // first op whose record is resident in d_rec
@@ -1047,30 +1063,56 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
         }
         const double *rec = s->d_rec + (jj - chunk0) * B * (size_t)s->rec_stride;
         if (use_tma) {
-            CK(s, cudaMemsetAsync(s->d_adj_part, 0, nblk_t * B * RED_NV * sizeof(double), s->stream));
-            int done[2] = {0, 0};   // X qubits per class already un-rotated in this factor group
-            for (int pi = 0; pi < np; ++pi) {
-                const int p = np - 1 - pi;
+            double *part_j = s->d_adj_part + (jj & 1) * region;
+            if (!carried) CK(s, cudaMemsetAsync(part_j, 0, region * sizeof(double), s->stream));
+            // X qubits per class already un-rotated in this factor group
+            int done[2] = {carried ? carry_done[0] : 0, carried ? carry_done[1] : 0};
+            bool next_carried = false;
+            for (int i = carried ? 1 : 0; i < np; ++i) {
+                const int p = share ? ord[dir][i] : np - 1 - i;
+                const bool last = i == np - 1;
                 TmaPass P = s->tpasses[NVAR * p + V_ROT];
-                P.frame = 1 | ((jj + 1 == nops && pi == 0) ? 2 : 0) | ((jj == 0 && pi == np - 1) ? 4 : 0);
-                const int zinv = (pi == 0 && ops[jj * B].has_z) ? 1 : 0;
-                P.xscale = (adj_tan && pi == 0 && !ops[jj * B].has_z) ? 1 : 0;
+                P.frame = 1 | ((jj + 1 == nops && i == 0) ? 2 : 0) | ((jj == 0 && last) ? 4 : 0);
+                const int zinv = (i == 0 && ops[jj * B].has_z) ? 1 : 0;
+                P.xscale = (adj_tan && i == 0 && !ops[jj * B].has_z) ? 1 : 0;
                 for (int stg = 0; stg < 3; ++stg) {          // stages run A, B, C
                     P.adj_u[stg][0] = s->nX0 - done[0];
                     P.adj_u[stg][1] = s->nX1 - done[1];
                     for (int kk = 0; kk < RB; ++kk)
                         if ((P.rot[stg] >> kk) & 1u) done[(P.cls[stg] >> kk) & 1u]++;
                 }
-                adj_kern<<<Gt, NT, adj_smem, s->stream>>>((float2 *)s->state[0], (float2 *)s->state[1], rec,
-                                                          s->rec_stride, s->n - LT, s->d_err, s->d_adj_part,
-                                                          (int)nblk_t, pi * (int)Gt, zinv, s->tmaps[p],
-                                                          s->tmaps_aux[p], P);
+                const bool merge = share && last && jj >= 1 && jj - 1 >= chunk0 && ops[(jj - 1) * B].has_z;
+                if (merge) {
+                    // last pass of op jj, Z layer and first pass of op jj-1 on the same qubits
+                    double *part_prev = s->d_adj_part + ((jj - 1) & 1) * region;
+                    const double *rec_prev = rec - B * (size_t)s->rec_stride;
+                    CK(s, cudaMemsetAsync(part_prev, 0, region * sizeof(double), s->stream));
+                    int d2[2] = {0, 0};
+                    for (int stg = 2; stg >= 0; --stg) {     // second round runs C, B, A
+                        P.adj_u2[stg][0] = s->nX0 - d2[0];
+                        P.adj_u2[stg][1] = s->nX1 - d2[1];
+                        for (int kk = 0; kk < RB; ++kk)
+                            if ((P.rot[stg] >> kk) & 1u) d2[(P.cls[stg] >> kk) & 1u]++;
+                    }
+                    carry_done[0] = d2[0];
+                    carry_done[1] = d2[1];
+                    adj_kern_m<<<Gt, NT, adj_smem, s->stream>>>(
+                        (float2 *)s->state[0], (float2 *)s->state[1], rec, s->rec_stride, s->n - LT, s->d_err, part_j,
+                        (int)nblk_t, i * (int)Gt, 0, rec_prev, part_prev, 0, s->tmaps[p], s->tmaps_aux[p], P);
+                    next_carried = true;
+                    dir ^= 1;
+                } else {
+                    adj_kern<<<Gt, NT, adj_smem, s->stream>>>(
+                        (float2 *)s->state[0], (float2 *)s->state[1], rec, s->rec_stride, s->n - LT, s->d_err, part_j,
+                        (int)nblk_t, i * (int)Gt, zinv, rec, part_j, 0, s->tmaps[p], s->tmaps_aux[p], P);
+                }
                 CKL(s); s->launches++;
             }
             if (done[0] != s->nX0 || done[1] != s->nX1)
                 FAIL(s, QS_ERR_STATE, "reverse passes do not cover every X qubit once");
-            k_finish<<<B, RED_THREADS, 0, s->stream>>>(s->d_adj_part, (int)nblk_t, 4, s->d_grad + jj * B * RED_NV);
+            k_finish<<<B, RED_THREADS, 0, s->stream>>>(part_j, (int)nblk_t, 4, s->d_grad + jj * B * RED_NV);
             CKL(s); s->launches++;
+            carried = next_carried;
             continue;
         }
         for (int pi = 0; pi < np; ++pi) {
@@ -1216,10 +1258,11 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
         cudaFuncSetAttribute(k_apply_h_pass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_apply_h_pass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_xmeasure<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((1 << LT) * 16));
-        for (int tn = 0; tn <= 1; ++tn) {
-            cudaFuncSetAttribute(adj_tma_kernel(2, tn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+        for (int v = 0; v < 3; ++v) {
+            const bool tn = v >= 1, mg = v == 2;
+            cudaFuncSetAttribute(adj_tma_kernel(2, tn, mg), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(4 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
-            cudaFuncSetAttribute(adj_tma_kernel(1, tn), cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(adj_tma_kernel(1, tn, mg), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(2 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
         }
     }

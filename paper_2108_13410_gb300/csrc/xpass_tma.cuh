@@ -58,6 +58,8 @@ struct TmaPass {
                                 // with a Z layer C is in the scaled table)
     int adj_u[3][2];            // adjoint, tangent form: X qubits of the factor group per
                                 // class not yet un-rotated when stage s reads its terms
+    int adj_u2[3][2];           // the same for the second round of a shared reverse pass
+                                // (the previous factor group; stages run C, B, A)
 };
 
 constexpr int TMA_TILE_BYTES = (1 << LT) * 8;

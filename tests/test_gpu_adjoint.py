@@ -142,19 +142,22 @@ def test_batched_complex64_adjoint_tma_path(L):
 @gpu
 @pytest.mark.parametrize("T,n", [(2.0, 16), (8.0, 8)])
 @pytest.mark.parametrize("adj", [0, 2])
-def test_complex64_adjoint_forms_and_buffers(T, n, adj):
+@pytest.mark.parametrize("merge", [1, 0])
+def test_complex64_adjoint_forms_and_buffers(T, n, adj, merge):
     """complex64 adjoint on the 3x2 torus in both forms of the reverse pass: small angles
     (T = 2, 16 steps) run the tangent form, large angles (T = 8, 8 steps: X angles
     near 1) the (u, s) rotations; with two and one tile buffers (QS_OPT_ADJOINT 0, 2).
     Gradient within 1e-3 of the largest oracle component, value within 1e-4 relative,
-    psi uncomputed back to |+> within 1e-4."""
-    from paper_2108_13410_gb300.qsim import QS_OPT_ADJOINT
+    psi uncomputed back to |+> within 1e-4.  With shared passes (QS_OPT_XMERGE 1) the
+    tangent-form reverse sweep shares one pass between consecutive factor groups."""
+    from paper_2108_13410_gb300.qsim import QS_OPT_ADJOINT, QS_OPT_XMERGE
     lat = OracleLattice(3, 2, True, "gh")
     c = Couplings(0.6, 0.6)
     s = O.schedule_fourier(T, n, synth.fourier_coeffs(4, seed=7, std=0.05))
     e_ref, g_ref = O.energy_gradient(lat, c, s, T / n, 2, np.eye(n))
     sim = _sim(3, 2, form="gh", dtype="c64", aux=True)
     sim.set_option(QS_OPT_ADJOINT, adj)
+    sim.set_option(QS_OPT_XMERGE, merge)
     for _ in range(2):                       # twice in a row: nothing left over between calls
         sim.init_plus()
         val, g = sim.adjoint_grad([(0.6, 0.6)], s, T / n, 2)
@@ -162,3 +165,25 @@ def test_complex64_adjoint_forms_and_buffers(T, n, adj):
         _close(g[0], g_ref, 1e-3)
         psi0 = sim.download()[0].numpy().astype(np.complex128)
         assert np.linalg.norm(psi0 - O.plus_state(lat.n_qubits)) <= 1e-4
+
+
+@gpu
+def test_shared_reverse_passes_across_a_record_chunk():
+    """3x2 torus (18 qubits, two passes per X layer), 2100 second-order steps (more than
+    the 2048 factor groups whose records are resident at once): the adjoint with shared
+    reverse passes gives the gradient of the adjoint with separate passes within 1e-3 of
+    its largest component, the complex64 tolerance (measured: 1.1e-4, rounding accumulated
+    over 2100 steps; a factor dropped or repeated at the chunk boundary, where the chain of
+    shared passes restarts, would differ by the size of the gradient), and the same value."""
+    from paper_2108_13410_gb300.qsim import QS_OPT_XMERGE
+    T, n = 42.0, 2100
+    s = O.schedule_linear(T, n)
+    res = []
+    for merge in (1, 0):
+        sim = _sim(3, 2, form="gh", dtype="c64", aux=True)
+        sim.set_option(QS_OPT_XMERGE, merge)
+        sim.init_plus()
+        res.append(sim.adjoint_grad([(0.6, 0.6)], s, T / n, 2))
+    (v1, g1), (v0, g0) = res
+    assert abs(v1[0] - v0[0]) <= 1e-4 * abs(v0[0])
+    _close(g1[0], g0[0], 1e-3)
