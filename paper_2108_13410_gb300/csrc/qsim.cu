@@ -1088,7 +1088,7 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
                     const double *rec_prev = rec - B * (size_t)s->rec_stride;
                     CK(s, cudaMemsetAsync(part_prev, 0, region * sizeof(double), s->stream));
                     int d2[2] = {0, 0};
-                    for (int stg = 2; stg >= 0; --stg) {     // second round runs C, B, A
+                    for (int stg = 2; stg >= 0; --stg) {     // second rotation round runs C, B, A
                         P.adj_u2[stg][0] = s->nX0 - d2[0];
                         P.adj_u2[stg][1] = s->nX1 - d2[1];
                         for (int kk = 0; kk < RB; ++kk)
