@@ -92,11 +92,10 @@ __device__ __forceinline__ void adj_rotate(u64 (&p)[NR], u64 (&l)[NR], unsigned 
     adj_rotate_t(p, l, mask, cls, C, corr, qi0, qi1, g0, g1);
 }
 
-// MERGED (tangent form only): a shared reverse pass over one qubit group G.  Its first
-// rotation round un-rotates X(G) of factor group j (terms to partials at slot0), then the
-// Z layer of group j-1 is undone in the stage-C layout (its terms and its scaled table,
-// recs2), and the second rotation round un-rotates X(G) of group j-1 in stages C, B, A
-// (terms to partials2 at slot0b)
+// MERGED (tangent form only): a shared reverse pass over one qubit group G.  Round 1
+// un-rotates X(G) of factor group j (terms to partials at slot0), then the Z layer of
+// group j-1 is undone in the stage-C layout (its terms and its scaled table, recs2), and
+// round 2 un-rotates X(G) of group j-1 in stages C, B, A (terms to partials2 at slot0b)
 // and stores from the stage-A layout.  Mirrors the shared passes of the forward sweep.
 template <int NBUF, bool TAN, bool MERGED>
 __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__restrict__ psi, float2 *__restrict__ lam,
@@ -367,7 +366,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
                     l[r] = pk(vl.x, vl.y);
                 }
             }
-            // ---- second rotation round: the previous group's X on the same qubits, stages C, B, A ----
+            // ---- round 2: the previous factor group's X on the same qubits, stages C, B, A ----
             adj_rotate(p, l, P.rot[2], cls2, RC2, corr2[2], qj0, qj1, g0b, g1b);
 #pragma unroll
             for (int r = 0; r < NR; ++r) { tp[c_base[r & 7] + (r << 4)] = p[r]; tl[c_base[r & 7] + (r << 4)] = l[r]; }
