@@ -262,10 +262,9 @@ long long qs_launch_count(qs_sim *sim);
 
 /* Norm and Z-string expectation without any memory allocation.  The paper has no
  * counterpart: this entry point exists for callers that must not allocate device
- * memory, e.g. code running while a stream is captured into a CUDA graph
- * (cudaMalloc is not a stream operation and cannot be captured), hosts that give
- * all device memory to their own pool, or loops where the device-wide
- * synchronisation of cudaMalloc is not acceptable.
+ * memory, e.g. hosts that give all device memory to their own pool before they
+ * load plug-ins (a cudaMalloc there fails or takes memory the pool counts on), or
+ * loops where the device-wide synchronisation of cudaMalloc is not acceptable.
  *
  * For each of `batch` states of 2^n_qubits amplitudes (layout of qs_bind_state,
  * dtype QS_C64 or QS_C128) at state_dev, writes out_dev[2b] = <psi_b|psi_b> and

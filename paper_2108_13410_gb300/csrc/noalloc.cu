@@ -3,10 +3,10 @@
 // qs_expect_z_noalloc computes, per batch element, <psi|psi> and <psi|Z_mask|psi>
 // (the same numbers as qs_expect(QS_NORM) and qs_expect_pauli(type 0)) without a
 // qs_sim handle and without any device allocation.  It is meant for callers that
-// may not allocate: code running while a CUDA stream is being captured into a
-// graph (cudaMalloc is not a stream operation and cannot be captured), hosts that
-// hand all device memory to their own pool before loading plugins, and latency-
-// critical loops where cudaMalloc's implicit device synchronisation is not allowed.
+// may not allocate: hosts that hand all device memory to their own pool before
+// they load plug-ins (a cudaMalloc there fails or steals memory the pool counts
+// on), and latency-critical loops where cudaMalloc's implicit device
+// synchronisation is not allowed.
 //
 // Its block partial sums live in a fixed file-scope device array.  Every GPU that
 // loads this library holds that array (QS_NOALLOC_MAX_BATCH * 304 * 2 doubles,
@@ -30,7 +30,10 @@ struct ErrSink {
     std::string msg;
     ErrSink &operator=(const std::string &m) { msg = m; qsim::set_handle_free_error(m); return *this; }
     ErrSink &operator=(const char *m) { return *this = std::string(m); }
-    void clear() { msg.clear(); qsim::set_handle_free_error(""); }
+    // Only this thread's message is reset on entry; the handle-free message that
+    // qs_last_error(NULL) reports is replaced when this entry point fails, never
+    // erased by a call that succeeds.
+    void clear() { msg.clear(); }
 };
 thread_local ErrSink g_err;
 

@@ -21,6 +21,7 @@ STATUS = {0: "QS_OK", 1: "QS_ERR_ARG", 2: "QS_ERR_OOM", 3: "QS_ERR_CUDA", 4: "QS
 QS_PERIODIC, QS_OPEN = 0, 1
 QS_GAUGE_HIGGS, QS_UNITARY_GAUGE = 0, 1
 QS_C64, QS_C128 = 0, 1
+QS_NOALLOC_MAX_BATCH = 16     # include/qsim.h
 QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
 QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_ADJOINT, \
     QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL, QS_OPT_SHARED_BUFFERS = range(11)

@@ -4,10 +4,14 @@ Tolerances (the stated accuracy targets of the build):
   amplitudes: ||psi - psi_ref|| / ||psi_ref|| <= 1e-10 (complex128), 1e-5 (complex64),
               and max_i |psi_i - psi_ref_i| <= tol * max_i |psi_ref_i|;
   observables bounded by 1 (plaquettes, Wilson and 't Hooft loops, <X>, <Q_v>):
-              1e-6 (complex128); complex64 uses |d<P>| <= 2 ||P|| ||d psi|| with
-              ||P|| = 1 and ||d psi|| <= 1e-5, i.e. 2e-5;
-  energies:   1e-6 absolute (complex128); complex64 uses the same bound
-              |dE| <= 2 ||H|| ||d psi|| with ||H|| <= sum of |coefficients|.
+              1e-6 (complex128); 2e-6 (complex64: about 3x the largest error measured
+              on these cases, 5.5e-7);
+  energies:   1e-6 absolute (complex128); complex64 1.2e-6 ||H|| with ||H|| <= the sum
+              of |coefficients| (the largest measured |dE| / ||H|| is 4e-7, on the
+              24-qubit unitary-gauge torus; 1e-7 to 2e-7 on these cases).
+  The complex64 bounds are set from measured errors so that a regression of a few
+  times in accuracy fails; the rigorous bound |d<P>| <= 2 ||P|| ||d psi|| with
+  ||d psi|| <= 1e-5 would hide a hundredfold one.
 """
 import numpy as np
 import pytest
@@ -43,12 +47,17 @@ def _h_norm_bound(lat, c, s=1.0):
             + len(lat.z_plaquettes()) * abs(coef["z_plaq"]) + len(lat.z_second()) * abs(coef["z_second"]))
 
 
+C64_OBS_TOL = 2e-6
+C64_ENERGY_PER_NORM = 1.2e-6
+C64_NORM_TOL = 1e-6        # measured |<psi|psi> - 1| <= 2.3e-7
+
+
 def _obs_tol(dtype):
-    return 1e-6 if dtype == "c128" else 2.0 * 1e-5
+    return 1e-6 if dtype == "c128" else C64_OBS_TOL
 
 
 def _energy_tol(dtype, lat, c):
-    return 1e-6 if dtype == "c128" else 2.0 * _h_norm_bound(lat, c) * 1e-5
+    return 1e-6 if dtype == "c128" else C64_ENERGY_PER_NORM * _h_norm_bound(lat, c)
 
 
 def _run_oracle(lat, c, s, dt, order):
@@ -98,7 +107,7 @@ def test_evolution_matches_oracle(case):
         assert abs(sim.expect(QS_X, q)[0] - obs["x"][q]) <= tol
     for v_, val in enumerate(obs["gauss"]):
         assert abs(sim.expect(QS_GAUSS, v_)[0] - val) <= tol
-    assert abs(sim.expect(QS_NORM)[0] - 1.0) <= (1e-12 if dtype == "c128" else 1e-5)
+    assert abs(sim.expect(QS_NORM)[0] - 1.0) <= (1e-12 if dtype == "c128" else C64_NORM_TOL)
 
 
 @gpu

@@ -168,7 +168,8 @@ def test_energy_from_tiled_x_measurement_matches_oracle():
     lat = OracleLattice(3, 2, True, "gh")
     s = O.schedule_linear(2.0, 20)
     ref = O.evolve(lat, Couplings(0.9, 0.4), s, 0.1, 2)
-    for dtype, tol in (("c128", 1e-9), ("c64", 1e-4)):
+    # complex64: measured 3.0e-6 (s = 1) and 2.6e-6 (s = 0.3)
+    for dtype, tol in (("c128", 1e-9), ("c64", 1e-5)):
         sim = _sim(3, 2, form="gh", dtype=dtype)
         sim.init_plus()
         sim.evolve([(0.9, 0.4)], s, 0.1, 2)
@@ -181,7 +182,8 @@ def test_energy_from_tiled_x_measurement_matches_oracle():
     sim = _sim(3, 3, form="gh", dtype="c64")
     sim.init_plus()
     sim.evolve([(0.6, 0.6)], s27, 0.02, 2)
-    assert abs(sim.energy([(0.6, 0.6)])[0] - O.energy(ref27, ug, Couplings(0.6, 0.6))) <= 2 * 50 * 1e-5
+    # complex64 after 10 steps: measured 7.0e-6
+    assert abs(sim.energy([(0.6, 0.6)])[0] - O.energy(ref27, ug, Couplings(0.6, 0.6))) <= 3e-5
 
 
 @gpu
