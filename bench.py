@@ -507,21 +507,30 @@ def ug32_leg(local, dev, stream):
 
 
 def protocol_leg(local, dev):
-    """The hysteresis run of Sec. IV at p = 0.5 on the 3x3 unitary-gauge torus (18
-    qubits, J = h = 1/2, dg = 1e-5, dt = 0.02, second order, complex64): psi_1 carried
-    O -> P -> P' and psi_1' carried O -> P' -> P, 100k steps per state; end energies next
-    to the printed ones.  Then the broken red paths of Sec. V (r = 0.05, 0.15, 0.25):
-    minimum of d^2E/dg^2 next to the printed one."""
+    """The hysteresis experiment of Sec. IV on the 3x3 unitary-gauge torus (18 qubits,
+    J = h = 1/2, dg = 1e-5, dt = 0.02, second order, complex64) at p = 0.12 (deconfined)
+    and p = 0.5: psi_1 carried O -> P -> P' and psi_1' carried O -> P' -> P, both energy
+    curves sampled along the blue path; E (psi_1 at P) and E' (psi_1' arrived at P) next
+    to the printed ones, with the crossing points.  Then the broken red paths of Sec. V
+    (r = 0.05, 0.15, 0.25): minimum of d^2E/dg^2 next to the printed one."""
     import torch
     from paper_2108_13410_gb300.reproduce import hysteresis, red_path_curvature
     torch.cuda.synchronize(dev)
-    r = hysteresis(0.5, 1e-5, 0.02)
-    r["steps_per_s"] = 2 * r["steps_per_state"] / r["seconds"]
+    out = {}
+    for p in (0.12, 0.5):
+        r = hysteresis(p, 1e-5, 0.02)
+        r.pop("curve")
+        if len(r["crossings"]) > 4:
+            r["crossings"] = "%d sign changes of a difference below %.1e" % (len(r["crossings"]),
+                                                                             r["max_abs_difference"])
+        r["steps_per_s"] = 2 * r["steps_per_state"] / r["seconds"]
+        out["hysteresis_p%03d" % round(100 * p)] = r
     red = []
     for rr in (0.05, 0.15, 0.25):
         c = red_path_curvature(rr)
         red.append({k: c[k] for k in ("r", "g_min", "printed_g_min", "d2E_min", "steps", "seconds")})
-    return {"hysteresis_p050": r, "red_paths": red}
+    out["red_paths"] = red
+    return out
 
 
 def adjoint_leg(n_steps, local, dev, stream):

@@ -19,6 +19,12 @@ __device__ __forceinline__ float rdot(u64 a, u64 b) {   // Re(conj(a) b) for pac
     return x.x * y.x + x.y * y.y;
 }
 
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
 __device__ __forceinline__ float idot(u64 l, u64 p) {   // Im(conj(l) p)
     const float2 x = unpk(l), y = unpk(p);
     return x.x * y.y - x.y * y.x;
@@ -82,6 +88,37 @@ __device__ __forceinline__ void adj_rotate_t(u64 (&p)[NR], u64 (&l)[NR], unsigne
     }
 }
 
+// Tangent form with the constants of each register bit read from a shared-memory table:
+// tc[k] = {(t, t), (-t, -t)} of the class of bit k, qi[k] = 1 / (1 + t^2) of that class;
+// corr is the scale correction at the start of the stage.  Terms of bits of class 1
+// (cls bit k set) go to g1, the others to g0.
+__device__ __forceinline__ void adj_rotate_ts(u64 (&p)[NR], u64 (&l)[NR], unsigned mask, unsigned cls,
+                                              const u64 (*tc)[2], const float *qi, float corr, float &g0,
+                                              float &g1) {
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+        const u64 pt = tc[k][0], nt = tc[k][1];
+        u64 accp = 0ull, accm = 0ull;   // (+0.0f, +0.0f)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if ((r >> k) & 1) continue;
+            const int q = r | (1 << k);
+            accp = fma2p(l[q], p[r], accp);
+            accm = fma2p(l[r], p[q], accm);
+            const u64 pa = p[r], pb = p[q], la = l[r], lb = l[q];
+            p[r] = fma2p(nt, pb, pa);
+            p[q] = fma2p(pt, pa, pb);
+            l[r] = fma2p(nt, lb, la);
+            l[q] = fma2p(pt, la, lb);
+        }
+        const float2 sp = unpk(accp), sm = unpk(accm);
+        const float g = ((sp.x + sp.y) - (sm.x + sm.y)) * corr;
+        if ((cls >> k) & 1u) g1 += g; else g0 += g;
+        corr *= qi[k];
+    }
+}
+
 __device__ __forceinline__ void adj_rotate(u64 (&p)[NR], u64 (&l)[NR], unsigned mask, const int (&cls)[RB],
                                            const RotConst &C, float, float, float, float &g0, float &g1) {
     adj_rotate_w(p, l, mask, cls, C, g0, g1);
@@ -97,6 +134,10 @@ __device__ __forceinline__ void adj_rotate(u64 (&p)[NR], u64 (&l)[NR], unsigned 
 // group j-1 is undone in the stage-C layout (its terms and its scaled table, recs2), and
 // round 2 un-rotates X(G) of group j-1 in stages C, B, A (terms to partials2 at slot0b)
 // and stores from the stage-A layout.  Mirrors the shared passes of the forward sweep.
+// Both tiles go back to HBM by bulk tensor stores from shared memory.  In the tangent
+// form the per-bit constants (t, -t), the 1 / (1 + t^2) factors and the per-stage scale
+// corrections of both rounds sit in a small shared-memory table (broadcast reads), which
+// keeps the kernel within 128 registers: two CTAs per SM with one tile-pair buffer each.
 template <int NBUF, bool TAN, bool MERGED>
 __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__restrict__ psi, float2 *__restrict__ lam,
                                                    const double *__restrict__ recs, int rec_stride, int tiles_shift,
@@ -116,6 +157,10 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
     __shared__ uint64_t bars[NBUF];
     __shared__ int s_ok;
     __shared__ double red[NT / 32][8];
+    __shared__ u64 s_tc[2][3][RB][2];     // TAN: per round, stage and register bit: (t,t), (-t,-t)
+    __shared__ float s_qi[2][3][RB];      // TAN: 1 / (1 + t^2) of that bit's class
+    __shared__ float s_corr[2][3];        // TAN: scale correction at the start of each stage
+    __shared__ float s_xs;                // TAN: C of the factor group (groups without Z layer)
 
     const int t = threadIdx.x;
     const long long G = gridDim.x;
@@ -144,6 +189,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
         int b = it % NBUF;
         int x2 = (int)(tile & ((1ll << P.mid_bits) - 1));
         int x4 = (int)(tile >> P.mid_bits);
+        bulk_wait_read_all();                // a store may still be reading this buffer
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive_expect_tx(&bars[b], 2 * TMA_TILE_BYTES);
         tma_load_5d(buf + (size_t)(2 * b) * (1 << LT), &tmap_p, &bars[b], 0, 0, x2, 0, x4);
@@ -155,57 +201,41 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
 
     const int tlo = t & 15, thi = t >> 4;
     const int a_base = swz128(t);
-    int c_base[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) c_base[j] = (tlo ^ (j << 1)) | (thi << 8);
     const int b_base = t << 3, b_x = t & 7;
-    long long toff = 0;
     uint32_t paA_t = 0, pbA_t = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        if ((tlo >> j) & 1) toff += P.toff_c[j];
-        if ((thi >> j) & 1) toff += P.toff_c[4 + j];
-    }
 #pragma unroll
     for (int j = 0; j < 8; ++j)
         if ((t >> j) & 1) { paA_t ^= P.paA_thr[j]; pbA_t ^= P.pbA_thr[j]; }
     const int nB1 = P.nB + 1, nlut = (P.nA + 1) * nB1;
     uint32_t paC_t = 0, pbC_t = 0;                   // MERGED: stage-C thread parity columns
-    long long toff_a = 0;                            // MERGED: stage-A store offset
     if (MERGED) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if ((tlo >> j) & 1) { paC_t ^= P.pa_thr[j]; pbC_t ^= P.pb_thr[j]; }
             if ((thi >> j) & 1) { paC_t ^= P.pa_thr[4 + j]; pbC_t ^= P.pb_thr[4 + j]; }
         }
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if ((t >> j) & 1) toff_a += P.toff_a[j];
     }
+    // stage-C shared-memory index of register r (128-byte swizzle)
+    auto c_idx = [&](int r) { return ((tlo ^ ((r & 7) << 1)) | (thi << 8)) + (r << 4); };
+    const long long tmask = (1ll << tiles_shift) - 1;
+    long long cur_batch = -1;
+    RotConst RC;                     // !TAN: (u, s) constants in registers
     int cls0[RB], cls1[RB], cls2[RB];
 #pragma unroll
     for (int kk = 0; kk < RB; ++kk) {
         cls0[kk] = (P.cls[0] >> kk) & 1; cls1[kk] = (P.cls[1] >> kk) & 1; cls2[kk] = (P.cls[2] >> kk) & 1;
     }
-    const long long tmask = (1ll << tiles_shift) - 1;
-    long long cur_batch = -1;
-    typedef typename std::conditional<TAN, TanConst, RotConst>::type XC;
-    XC RC;
-    float corr[3] = {1.f, 1.f, 1.f};
-    float qi0 = 1.f, qi1 = 1.f;     // 1 / (1 + t^2) per class
-    float xs = 1.f;
-    XC RC2;                          // MERGED: the previous factor group's constants
-    float corr2[3] = {1.f, 1.f, 1.f};
-    float qj0 = 1.f, qj1 = 1.f;
     constexpr int NV = MERGED ? 8 : 4;
-    double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    // block sums of one batch element: values 0..3 to partials, 4..7 (MERGED) to partials2
+    // FP64 block sums of one batch element accumulate in per-warp shared-memory slots
+    // (red[w][v], lane 0 of warp w adds the warp's per-tile float sum), so no FP64
+    // accumulator occupies registers across tiles
+    for (int e = t; e < (NT / 32) * 8; e += NT) red[e / 8][e % 8] = 0.0;
+    auto add_tile = [&](int v, float x) {
+        x = warp_sum_f(x);
+        if ((t & 31) == 0) red[t >> 5][v] += (double)x;
+    };
+    // values 0..3 to partials, 4..7 (MERGED) to partials2
     auto flush = [&](long long bat) {
-        __syncthreads();
-        for (int v = 0; v < NV; ++v) {
-            double x = warp_sum(acc[v]);
-            if ((t & 31) == 0) red[t >> 5][v] = x;
-        }
         __syncthreads();
         if (t < NV) {
             double sum = 0.0;
@@ -213,7 +243,13 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
             if (t < 4) partials[(bat * nblk + slot0 + blockIdx.x) * RED_NV + t] = sum;
             else partials2[(bat * nblk + slot0b + blockIdx.x) * RED_NV + (t - 4)] = sum;
         }
-        for (int v = 0; v < 8; ++v) acc[v] = 0.0;
+        __syncthreads();
+        for (int e = t; e < (NT / 32) * 8; e += NT) red[e / 8][e % 8] = 0.0;
+    };
+    // one un-rotation stage on both tiles (table-driven in the tangent form)
+    auto unrot = [&](int round, int st, const int (&cls)[RB], float &g0, float &g1, u64 (&p)[NR], u64 (&l)[NR]) {
+        if (TAN) adj_rotate_ts(p, l, P.rot[st], P.cls[st], s_tc[round][st], s_qi[round][st], s_corr[round][st], g0, g1);
+        else adj_rotate_w(p, l, P.rot[st], cls, RC, g0, g1);
     };
 
     long long tile = first;
@@ -225,34 +261,39 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
             if (cur_batch >= 0) flush(cur_batch);   // the previous batch element's sums
             __syncthreads();
             const double *rec = recs + batch * rec_stride;
-            load_xconst(RC, rec, P.tan_off);
-            if (TAN) {
-                const double q0 = 1.0 + rec[P.tan_off] * rec[P.tan_off];
-                const double q1 = 1.0 + rec[P.tan_off + 1] * rec[P.tan_off + 1];
-                for (int st = 0; st < 3; ++st)
-                    corr[st] = (float)(pow(q0, (double)P.adj_u[st][0]) * pow(q1, (double)P.adj_u[st][1]));
-                qi0 = (float)(1.0 / q0);
-                qi1 = (float)(1.0 / q1);
-                xs = (float)rec[P.tan_off + 2];
+            if (!TAN) load_xconst(RC, rec, P.tan_off);
+            if (TAN && t < 2 * 3 * RB) {
+                // round 0: this factor group (stages A, B, C), round 1 (MERGED): the
+                // previous one (stages C, B, A); inverse factor: a' = a - t b, b' = b + t a
+                const int round = t / (3 * RB), st = (t / RB) % 3, k = t % RB;
+                if (round == 0 || MERGED) {
+                    const double *rr = round ? recs2 + batch * rec_stride : rec;
+                    const int c = (P.cls[st] >> k) & 1;
+                    const double tv = rr[P.tan_off + c];
+                    s_tc[round][st][k][0] = pk((float)tv, (float)tv);
+                    s_tc[round][st][k][1] = pk(-(float)tv, -(float)tv);
+                    s_qi[round][st][k] = (float)(1.0 / (1.0 + tv * tv));
+                    if (k == 0) {
+                        const double q0 = 1.0 + rr[P.tan_off] * rr[P.tan_off];
+                        const double q1 = 1.0 + rr[P.tan_off + 1] * rr[P.tan_off + 1];
+                        const int *u = round ? P.adj_u2[st] : P.adj_u[st];
+                        s_corr[round][st] = (float)(pow(q0, (double)u[0]) * pow(q1, (double)u[1]));
+                    }
+                }
             }
+            if (TAN && t == 0) s_xs = (float)rec[P.tan_off + 2];
             if (zinv) {   // inverse Z layer: conjugated phase table (tangent form: scaled by C)
                 const int loff = TAN ? P.tan_off + 4 : 4;
                 for (int i = t; i < nlut; i += NT)
                     lut[i] = make_float2((float)rec[loff + 2 * i], -(float)rec[loff + 2 * i + 1]);
             }
-            if (MERGED) {   // the previous factor group: constants, scale corrections, Z table
+            if (MERGED) {   // the previous factor group's scaled Z table
                 const double *rec2 = recs2 + batch * rec_stride;
-                load_xconst(RC2, rec2, P.tan_off);
-                const double q0 = 1.0 + rec2[P.tan_off] * rec2[P.tan_off];
-                const double q1 = 1.0 + rec2[P.tan_off + 1] * rec2[P.tan_off + 1];
-                for (int st = 0; st < 3; ++st)
-                    corr2[st] = (float)(pow(q0, (double)P.adj_u2[st][0]) * pow(q1, (double)P.adj_u2[st][1]));
-                qj0 = (float)(1.0 / q0);
-                qj1 = (float)(1.0 / q1);
                 for (int i = t; i < nlut; i += NT)
                     lut[i] = make_float2((float)rec2[P.tan_off + 4 + 2 * i], -(float)rec2[P.tan_off + 5 + 2 * i]);
             }
             cur_batch = batch;
+            __syncthreads();
         }
         if (NBUF == 1) {
             __syncthreads();                 // the single buffer is free again
@@ -262,8 +303,9 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
             if (!mbar_wait_bounded(&bars[b], parity, max_wait)) {
                 atomicOr(err_flag, 1);
                 s_ok = 0;
-                for (int j = it; j < it + (NBUF > 1 ? NBUF - 1 : 1) && j < n_my; ++j)
+                for (int j = it + 1; j < it + NBUF - 1 && j < n_my; ++j)
                     mbar_wait_bounded(&bars[j % NBUF], (uint32_t)((j / NBUF) & 1), max_wait);
+                bulk_wait_all();
             }
         }
         __syncthreads();
@@ -295,6 +337,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
             }
         }
         if (TAN && !zinv && P.xscale) {   // C of a factor group without Z layer
+            const float xs = s_xs;
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
                 const float2 vp = unpk(p[r]), vl = unpk(l[r]);
@@ -311,7 +354,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
                 l[r] = pk(vl.x, vl.y);
             }
         }
-        adj_rotate(p, l, P.rot[0], cls0, RC, corr[0], qi0, qi1, g0, g1);
+        unrot(0, 0, cls0, g0, g1, p, l);
 #pragma unroll
         for (int r = 0; r < NR; ++r) { tp[a_base + (r << TB)] = p[r]; tl[a_base + (r << TB)] = l[r]; }
         __syncthreads();
@@ -324,7 +367,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
                 p[2 * m] = qp.x; p[2 * m + 1] = qp.y;
                 l[2 * m] = ql.x; l[2 * m + 1] = ql.y;
             }
-            adj_rotate(p, l, P.rot[1], cls1, RC, corr[1], qi0, qi1, g0, g1);
+            unrot(0, 1, cls1, g0, g1, p, l);
 #pragma unroll
             for (int m = 0; m < NR / 2; ++m) {
                 tp2[b_base + (m ^ b_x)] = make_ulonglong2(p[2 * m], p[2 * m + 1]);
@@ -334,8 +377,8 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
         }
         // ---- stage C ----
 #pragma unroll
-        for (int r = 0; r < NR; ++r) { p[r] = tp[c_base[r & 7] + (r << 4)]; l[r] = tl[c_base[r & 7] + (r << 4)]; }
-        adj_rotate(p, l, P.rot[2], cls2, RC, corr[2], qi0, qi1, g0, g1);
+        for (int r = 0; r < NR; ++r) { p[r] = tp[c_idx(r)]; l[r] = tl[c_idx(r)]; }
+        unrot(0, 2, cls2, g0, g1, p, l);
         if (P.frame & 4) {
             const int k0 = -(__popc(tlo) + __popc(thi) + pc_tile);
 #pragma unroll
@@ -346,8 +389,6 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
                 l[r] = pk(vl.x, vl.y);
             }
         }
-        const long long mid = tile & ((1ll << P.mid_bits) - 1);
-        const long long up = tile >> P.mid_bits;
         if (MERGED) {
             // ---- the previous factor group's Z layer, undone in the stage-C layout ----
             float g0b = 0.f, g1b = 0.f, ga2 = 0.f, gb2 = 0.f;
@@ -367,9 +408,9 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
                 }
             }
             // ---- round 2: the previous factor group's X on the same qubits, stages C, B, A ----
-            adj_rotate(p, l, P.rot[2], cls2, RC2, corr2[2], qj0, qj1, g0b, g1b);
+            unrot(1, 2, cls2, g0b, g1b, p, l);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) { tp[c_base[r & 7] + (r << 4)] = p[r]; tl[c_base[r & 7] + (r << 4)] = l[r]; }
+            for (int r = 0; r < NR; ++r) { tp[c_idx(r)] = p[r]; tl[c_idx(r)] = l[r]; }
             __syncthreads();
             if (P.stage_b) {
                 ulonglong2 *tp2 = reinterpret_cast<ulonglong2 *>(tp), *tl2 = reinterpret_cast<ulonglong2 *>(tl);
@@ -379,7 +420,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
                     p[2 * m] = qp.x; p[2 * m + 1] = qp.y;
                     l[2 * m] = ql.x; l[2 * m + 1] = ql.y;
                 }
-                adj_rotate(p, l, P.rot[1], cls1, RC2, corr2[1], qj0, qj1, g0b, g1b);
+                unrot(1, 1, cls1, g0b, g1b, p, l);
 #pragma unroll
                 for (int m = 0; m < NR / 2; ++m) {
                     tp2[b_base + (m ^ b_x)] = make_ulonglong2(p[2 * m], p[2 * m + 1]);
@@ -389,24 +430,30 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
             }
 #pragma unroll
             for (int r = 0; r < NR; ++r) { p[r] = tp[a_base + (r << TB)]; l[r] = tl[a_base + (r << TB)]; }
-            adj_rotate(p, l, P.rot[0], cls0, RC2, corr2[0], qj0, qj1, g0b, g1b);
-            const long long gbase = (mid << P.c) + (up << (P.next + P.k)) + toff_a;
-            u64 *dp = reinterpret_cast<u64 *>(psi + gbase);
-            u64 *dl = reinterpret_cast<u64 *>(lam + gbase);
+            unrot(1, 0, cls0, g0b, g1b, p, l);
+            // back into the stage-A positions of the swizzled tiles
 #pragma unroll
-            for (int r = 0; r < NR; ++r) { dp[P.roff_a[r]] = p[r]; dl[P.roff_a[r]] = l[r]; }
-            acc[0] += (double)g0; acc[1] += (double)g1;
-            acc[4] += (double)g0b; acc[5] += (double)g1b; acc[6] += (double)ga2; acc[7] += (double)gb2;
+            for (int r = 0; r < NR; ++r) { tp[a_base + (r << TB)] = p[r]; tl[a_base + (r << TB)] = l[r]; }
+            add_tile(0, g0); add_tile(1, g1);
+            add_tile(4, g0b); add_tile(5, g1b); add_tile(6, ga2); add_tile(7, gb2);
         } else {
-            const long long gbase = (mid << P.c) + (up << (P.next + P.k)) + toff;
-            u64 *dp = reinterpret_cast<u64 *>(psi + gbase);
-            u64 *dl = reinterpret_cast<u64 *>(lam + gbase);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) { dp[P.roff_c[r]] = p[r]; dl[P.roff_c[r]] = l[r]; }
-            acc[0] += (double)g0; acc[1] += (double)g1; acc[2] += (double)ga; acc[3] += (double)gb;
+            for (int r = 0; r < NR; ++r) { tp[c_idx(r)] = p[r]; tl[c_idx(r)] = l[r]; }
+            add_tile(0, g0); add_tile(1, g1); add_tile(2, ga); add_tile(3, gb);
+        }
+        // both tiles back to HBM by bulk tensor stores (same maps and boxes as the loads)
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (t == 0) {
+            const int x2 = (int)(tile & ((1ll << P.mid_bits) - 1));
+            const int x4 = (int)(tile >> P.mid_bits);
+            tma_store_5d(&tmap_p, tp, 0, 0, x2, 0, x4);
+            tma_store_5d(&tmap_l, tl, 0, 0, x2, 0, x4);
+            bulk_commit();
         }
     }
     if (cur_batch >= 0) flush(cur_batch);   // the last batch element's sums
+    if (t == 0) bulk_wait_all();            // the CTA's shared memory must outlive its stores
 }
 
 }  // namespace qsim

@@ -4,12 +4,13 @@ on the GPU.
     python -m paper_2108_13410_gb300.reproduce [--p 0.12 0.50] [--dg 1e-5] [--dt 0.02]
                                                [--red 0.05 0.15 0.25] [--table1]
 
-3x3 torus, unitary-gauge form (18 link qubits), J = h = 1/2.  E: psi_1 prepared at O is
-carried along the g axis to P(p, 0), then along the blue path to P'(0, p); E': psi_1'
+3x3 torus, unitary-gauge form (18 link qubits), J = h = 1/2.  psi_1 prepared at O is
+carried along the g axis to P(p, 0), then along the blue path to P'(0, p); psi_1'
 prepared at O is carried along the lambda axis to P'(0, p), then back along the blue
-path to P(p, 0).  The energies at the path ends are printed next to the values quoted
-in the hysteresis figure (dg = 1e-5, dt = 2e-2 per step, second-order Trotter, as stated
-for the paper's runs).  Prints one JSON line.
+path to P(p, 0).  Both energy curves are sampled along the blue path; E (psi_1 at P)
+and E' (psi_1' after arriving at P) are printed next to the values quoted in the
+hysteresis figure (dg = 1e-5, dt = 2e-2 per step, second-order Trotter, as stated for
+the paper's runs), with the crossing points of the two curves.  Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -20,32 +21,68 @@ import time
 PRINTED = {0.12: (-9.16003, -9.15039), 0.50: (-14.06553, -14.06550)}
 
 
+def _sample_every(n: int, samples: int = 48) -> int:
+    """Steps between energy samples: a divisor of n close to n / samples."""
+    d = max(1, n // samples)
+    while n % d:
+        d -= 1
+    return d
+
+
 def hysteresis(p: float, dg: float, dt: float, dtype: str = "c64", order: int = 2, renorm_every: int = 100,
-               options: dict | None = None):
-    """Energies at the ends of the two hysteresis paths.  renorm_every > 0 renormalises
-    the state every that many steps: over 10^5 steps the phase tables' residual modulus
-    errors (~1e-10 each, correlated while the couplings change slowly) would otherwise
-    move the norm by ~1e-5.  options: further {QS_OPT_*: value} for the simulator."""
+               samples: int = 48, options: dict | None = None):
+    """The history dependence of Sec. IV on the blue path, as two energy curves.
+
+    psi_1 (Eq. (14)) is carried from O along the g axis to P(p, 0), then along the blue
+    path to P'(0, p); psi_1' (Eq. (15)) is carried along the lambda axis to P'(0, p), then
+    along the blue path back to P.  Both energies <H1> are sampled at the same lambda
+    values (every few steps, both path ends included).  The printed pair is read at the
+    same parameter point P: E is the energy of psi_1 as prepared at P (the start of its
+    curve), E' the energy of psi_1' after it arrives at P (the end of its curve).  Reading
+    the two path ends instead (psi_1 at P', psi_1' at P) compares mirror images: on the
+    self-dual torus with J = h the two processes map onto each other, so those energies
+    agree up to the Trotter ordering whatever the phase.
+
+    Returns E, E', both curves (lambda, E(lambda), E'(lambda)), and the lambda values where
+    E - E' changes sign (linear interpolation between samples).  renorm_every > 0
+    renormalises the state every that many steps: over 10^5 steps the phase tables'
+    residual modulus errors (~1e-10 each, correlated while the couplings change slowly)
+    would otherwise move the norm by ~1e-5.  options: further {QS_OPT_*: value}."""
+    import numpy as np
     from . import Simulator, QS_OPT_RENORM_EVERY
-    from .protocol import prepare, blue
+    from .protocol import prepare, blue, run_path
     out = {"p": p, "dtype": dtype, "renorm_every": renorm_every}
     t0 = time.perf_counter()
     sim = Simulator(3, 3, form="ug", dtype=dtype)
     sim.set_option(QS_OPT_RENORM_EVERY, renorm_every)
     for key, value in (options or {}).items():
         sim.set_option(key, value)
+    fwd, back = blue(p, dg), blue(p, dg, reverse=True)
+    every = _sample_every(len(fwd), samples)
+    # psi_1: O -> P, then P -> P'
     sim.init_toric(0)
     sim.evolve_path(prepare(p, dg, "g"), dt, order)
-    path = blue(p, dg)
-    sim.evolve_path(path, dt, order)
-    out["E"] = float(sim.energy([path[-1]])[0])
+    e1 = [float(sim.energy([(p, 0.0, 0.5, 0.5)])[0])]
+    e1 += [e for _, e in run_path(sim, fwd, dt, order, measure_every=every)]
+    # psi_1': O -> P', then P' -> P
     sim.init_toric(1)
     sim.evolve_path(prepare(p, dg, "lambda"), dt, order)
-    path = blue(p, dg, reverse=True)
-    sim.evolve_path(path, dt, order)
-    out["E_prime"] = float(sim.energy([path[-1]])[0])
-    out["steps_per_state"] = len(prepare(p, dg)) + len(path)
-    out["seconds"] = time.perf_counter() - t0
+    e2 = [float(sim.energy([(0.0, p, 0.5, 0.5)])[0])]
+    e2 += [e for _, e in run_path(sim, back, dt, order, measure_every=every)]
+    lam = np.linspace(0.0, p, len(e1))
+    E1 = np.array(e1)
+    E2 = np.array(e2[::-1])                 # on the same lambda grid
+    D = E1 - E2
+    cross = []
+    for i in range(len(D) - 1):
+        if D[i] == 0.0 or D[i] * D[i + 1] < 0.0:
+            cross.append(float(lam[i] + (lam[i + 1] - lam[i]) * D[i] / (D[i] - D[i + 1])))
+    out.update({"E": float(E1[0]), "E_prime": float(E2[0]),
+                "E_at_P_prime": float(E1[-1]), "E_prime_at_P_prime": float(E2[-1]),
+                "crossings": cross, "max_abs_difference": float(np.max(np.abs(D))),
+                "curve": {"lambda": lam.tolist(), "E": E1.tolist(), "E_prime": E2.tolist()},
+                "steps_per_state": len(prepare(p, dg)) + len(fwd), "sample_every": every,
+                "seconds": time.perf_counter() - t0})
     if p in PRINTED:
         out["printed_E"], out["printed_E_prime"] = PRINTED[p]
     return out

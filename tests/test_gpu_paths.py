@@ -10,6 +10,9 @@ from oracle import core as O
 
 gpu = pytest.mark.gpu
 
+# |E - E'| at p = 0.12: far above the complex64 energy error (~1e-5)
+HYST_GAP_MIN = 1e-3
+
 
 def _sim(*a, **k):
     from paper_2108_13410_gb300 import Simulator
@@ -84,14 +87,37 @@ def test_adjoint_over_more_than_one_record_chunk():
 def test_hysteresis_run_complex64_matches_complex128():
     """The hysteresis protocol of Sec. IV at p = 0.5 with a coarser dg = 5e-4 (1000 +
     1000 steps per state): complex64 with renormalisation every 100 steps (the driver's
-    default) gives the complex128 end energies to 5e-6; both lie above the ground energy
-    of the 3x3 unitary-gauge torus at (0, 0.5) and (0.5, 0), which is below -14.0656."""
+    default) gives the complex128 energies to 5e-6 along both curves; E and E' (both
+    read at P) lie above the ground energy of the 3x3 unitary-gauge torus at (0.5, 0),
+    which is below -14.0656."""
     from paper_2108_13410_gb300.reproduce import hysteresis
     r64 = hysteresis(0.5, 5e-4, 0.02, "c64")
     r128 = hysteresis(0.5, 5e-4, 0.02, "c128", renorm_every=0)
-    assert abs(r64["E"] - r128["E"]) <= 5e-6
-    assert abs(r64["E_prime"] - r128["E_prime"]) <= 5e-6
-    assert r128["E"] >= -14.065684 and r128["E_prime"] >= -14.065684
+    for key in ("E", "E_prime"):
+        assert abs(r64[key] - r128[key]) <= 5e-6
+        assert r128[key] >= -14.065684
+        assert np.max(np.abs(np.array(r64["curve"][key]) - np.array(r128["curve"][key]))) <= 5e-6
+
+
+@gpu
+def test_hysteresis_curves_cross_only_in_the_deconfined_phase():
+    """Sec. IV: inside the deconfined phase (p = 0.12) psi_1 and psi_1' stay in different
+    topological sectors, so the energies of the two states at the same point differ
+    (E != E' at P, and the mirror difference at P') and the two curves cross; outside it
+    (p = 0.5) the curves nearly coincide.  On the self-dual torus the crossing sits at the
+    middle of the blue path.  dt = 0.02, complex64 renormalised every 100 steps; dg = 1e-4
+    at p = 0.12 (measured gap 0.024, crossing at lambda = 0.0600) and the paper's 1e-5 at
+    p = 0.5 (a faster sweep is not adiabatic across the transition near g = 0.2; measured
+    largest difference 2.9e-6)."""
+    from paper_2108_13410_gb300.reproduce import hysteresis
+    r = hysteresis(0.12, 1e-4, 0.02, "c64")
+    gap_P = r["E_prime"] - r["E"]                      # psi_1' arrives above psi_1 at P
+    gap_Pp = r["E_at_P_prime"] - r["E_prime_at_P_prime"]
+    assert gap_P >= HYST_GAP_MIN and gap_Pp >= HYST_GAP_MIN, (gap_P, gap_Pp)
+    assert abs(gap_P - gap_Pp) <= 1e-3                 # mirror images (Trotter ordering only)
+    assert len(r["crossings"]) == 1 and abs(r["crossings"][0] - 0.06) <= 0.01, r["crossings"]
+    q = hysteresis(0.5, 1e-5, 0.02, "c64")
+    assert q["max_abs_difference"] <= 1e-4, q["max_abs_difference"]
 
 
 @gpu
