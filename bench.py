@@ -258,6 +258,8 @@ def run_ours(args):
     cpl = [(W["g"], W["lam"])]
     sim = Simulator(W["Lx"], W["Ly"], form=W["form"], dtype=W["dtype"], device=f"cuda:{local}")
     stream = torch.cuda.current_stream(dev)
+    # autotuner: pass plan (qubits fused per X pass), then the X-pass kernel configuration
+    tune = sim.autotune(n_steps=20, cache=False)
     sim.init_plus()
     # warm-up
     sim.evolve(cpl, sched[:Wu], dt, W["order"])
@@ -288,7 +290,13 @@ def run_ours(args):
     state_bytes = sim.state_bytes
     alg_bytes = 2.0 * state_bytes                     # one read + one write of the state per pass
     peak, peak_kind = peaks()
-    names = ("k_xpass_tma<3, true, false, true>", "k_xpass_tma<2, true, true, true>")
+    # the two X-pass kernels the tuned configuration runs (tangent form; shared passes
+    # default to two tile buffers in the gauge-Higgs form)
+    tb = lambda v: "true" if v else "false"
+    names = ("k_xpass_tma<%d, %s, false, true>" % (tune["buffers"], tb(tune["store"])),
+             "k_xpass_tma<%d, %s, true, true>" % (tune["shared_buffers"] or 2, tb(tune["store"])))
+    if tune["xpass"] == 1:                            # the register-staged kernel (no shared passes)
+        names = ("k_xpass<float>", "k_xpass<float>")
     tags = ("k_xpass_tma_c64_27q", "k_xpass_tma_shared_c64_27q")
     dom = 0 if kinds[0][0] >= kinds[1][0] else 1     # dominant kernel: larger total time
     per_kind = {}
@@ -373,7 +381,11 @@ def run_ours(args):
                "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
                "config": workload_config(world),
                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-               "clocks": clk}
+               "clocks": clk,
+               "tuning": {"plan_qubits_per_pass": tune["plan"], "xpass_kernel": tune["xpass"],
+                          "tile_buffers": tune["buffers"], "bulk_store": tune["store"],
+                          "shared_pass_buffers": tune["shared_buffers"],
+                          "tuned_ms_per_step": tune["ms_per_step"]}}
         out.update(extra)
         print(json.dumps(out))
     if world > 1:

@@ -110,11 +110,19 @@ typedef enum {
                                  scheduled and sets up while the previous kernel
                                  drains and waits for its writes before reading
                                  global memory; 0: plain stream order             */
-    QS_OPT_SHARED_BUFFERS = 10 /* tile buffers per CTA of the shared X passes
+    QS_OPT_SHARED_BUFFERS = 10, /* tile buffers per CTA of the shared X passes
                                  (QS_OPT_XMERGE): 2 (three CTAs per SM), 3 (two CTAs
                                  per SM) or 0 (default): 2 for tangent-form rotations
                                  (gauge-Higgs), 3 for Walsh-Hadamard passes (unitary
                                  gauge), the faster of the two for each as measured */
+    QS_OPT_PLAN = 11          /* pass plan of the tiled X layer: how many new qubits
+                                 each pass after the first fuses (the first pass always
+                                 takes qubits 0..11).  Value: one 4-bit field per pass,
+                                 lowest first, each in [1, 8], summing to n - 12 (a pass
+                                 fusing k new qubits keeps a contiguous chunk of 12 - k
+                                 low qubits, 2^(12-k) amplitudes per row); 0 (default):
+                                 8 per pass, the remainder last.  Rejected (QS_ERR_ARG)
+                                 for states of fewer than 13 qubits.                  */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open
@@ -232,6 +240,20 @@ qs_status qs_dos(qs_sim *sim, double *out);
  * Outputs the choice and its ms per step (host). */
 qs_status qs_autotune(qs_sim *sim, int n_steps, int *best_xpass, int *best_buffers, int *best_store,
                       int *best_shared_buffers, double *best_ms_per_step);
+
+/* Pass-plan autotuner (the fusion width of the tiled X layer): times n_steps
+ * second-order steps with every plan of the fewest passes whose passes each fuse 4 to 8
+ * new qubits (rows of 128 B to 2 KB), on the bound state, which is overwritten, and keeps
+ * the fastest (QS_OPT_PLAN).  Writes the qubits fused by each pass (the first pass 12)
+ * to qubits_per_pass[0 .. *n_passes - 1] (host, at most max entries) and the best ms per
+ * step.  QS_ERR_ARG for fewer than 13 qubits or max too small. */
+qs_status qs_autotune_plan(qs_sim *sim, int n_steps, int *qubits_per_pass, int max, int *n_passes,
+                           double *best_ms_per_step);
+
+/* The current pass plan: qubits fused by each tiled X pass (the first 12), host output of
+ * at most max entries; returns the number of passes (0 for states smaller than one tile,
+ * -1 on a bad argument). */
+int qs_plan(const qs_sim *sim, int *qubits_per_pass, int max);
 
 /* Failure-detection self-test: launches a kernel that waits on an mbarrier which
  * never completes, with the same bounded wait as the TMA X pass, limited to

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <functional>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -68,6 +69,9 @@ struct qs_sim {
     int nA = 0, nB = 0, rec_stride = 0;
     int nXA = 0, nXB = 0, xlut_off = 0;    // Hadamard-basis X table (unitary gauge)
     int max_lut = 0;                       // largest phase table (entries)
+    std::vector<int> plan_k;               // new qubits of each pass after the first (empty: 8 per pass)
+    std::vector<int> pass_q;               // qubits fused by each pass of the current plan
+    long long plan_code = 0;               // QS_OPT_PLAN value of plan_k (0: default)
     std::vector<PassDesc> passes;          // pass plan (Z columns, no phase)
     std::vector<PassDesc> pvar;            // [NVAR * pass + variant]
     PassDesc *d_passes = nullptr;          // device copy of pvar
@@ -151,14 +155,18 @@ namespace {
 void build_passes(qs_sim *s) {
     const int n = s->n;
     s->passes.clear();
+    s->pass_q.clear();
     if (n < LT) return;
     int next = 0;
+    size_t pi = 0;   // index into plan_k
     while (next < n) {
         PassDesc d;
         memset(&d, 0, sizeof(d));
         d.n = n;
         int first = (next == 0);
-        int k = first ? LT : std::min(8, n - next);
+        int k = first ? LT : (pi < s->plan_k.size() ? s->plan_k[pi] : std::min(8, n - next));
+        if (!first) ++pi;
+        s->pass_q.push_back(k);
         int c = LT - k;                 // chunk bits (already rotated)
         bool rot_local[LT];
         for (int j = 0; j < LT; ++j) {
@@ -332,6 +340,25 @@ qs_status encode_tmaps(qs_sim *s, int slot = 0) {
         maps.push_back(m);
     }
     ok = true;
+    return QS_OK;
+}
+
+// Rebuild the pass tables after a change of plan_k: host descriptors, their device copy,
+// the tensor maps of the bound states; the cached evolve graph holds the old ones.
+qs_status rebuild_plan(qs_sim *s) {
+    if (s->stream) CK(s, cudaStreamSynchronize(s->stream));
+    build_passes(s);
+    build_variants(s);
+    build_tma_passes(s);
+    if (s->d_passes) { CK(s, cudaFree(s->d_passes)); s->d_passes = nullptr; }
+    if (!s->pvar.empty()) {
+        CK(s, cudaMalloc((void **)&s->d_passes, s->pvar.size() * sizeof(PassDesc)));
+        CK(s, cudaMemcpy(s->d_passes, s->pvar.data(), s->pvar.size() * sizeof(PassDesc), cudaMemcpyHostToDevice));
+    }
+    if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
+    qs_status st;
+    if (s->state[0] && (st = encode_tmaps(s, 0)) != QS_OK) return st;
+    if (s->state[1] && (st = encode_tmaps(s, 1)) != QS_OK) return st;
     return QS_OK;
 }
 
@@ -1360,6 +1387,24 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
         case QS_OPT_TMA_BUFFERS:
             if (value != 2 && value != 3) FAIL(s, QS_ERR_ARG, "TMA buffers must be 2 or 3");
             s->nbuf = (int)value; return QS_OK;
+        case QS_OPT_PLAN: {
+            if (s->n <= LT) FAIL(s, QS_ERR_ARG, "a pass plan needs more than %d qubits", LT);
+            if (value < 0) FAIL(s, QS_ERR_ARG, "bad plan");
+            std::vector<int> k;
+            int sum = 0;
+            for (long long v = value; v; v >>= 4) {
+                const int x = (int)(v & 15);
+                if (x < 1 || x > 8) FAIL(s, QS_ERR_ARG, "each pass of a plan fuses 1 to 8 new qubits");
+                k.push_back(x);
+                sum += x;
+            }
+            if (value != 0 && sum != s->n - LT)
+                FAIL(s, QS_ERR_ARG, "the plan fuses %d new qubits, the state has %d beyond the first pass", sum,
+                     s->n - LT);
+            s->plan_k = k;
+            s->plan_code = value;
+            return rebuild_plan(s);
+        }
         default: FAIL(s, QS_ERR_ARG, "unknown option %d", key);
     }
 }
@@ -1808,6 +1853,82 @@ qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers
     s->xpass_impl = pick.xpass; s->nbuf = pick.nbuf; s->tma_store = pick.store; s->nbuf_shared = pick.nsh;
     *best_xpass = pick.xpass; *best_buffers = pick.nbuf; *best_store = pick.store;
     *best_shared_buffers = pick.nsh;
+    *best_ms_per_step = best / n_steps;
+    return QS_OK;
+}
+
+int qs_plan(const qs_sim *s, int *qubits_per_pass, int max) {
+    if (!s || max < 0 || (max > 0 && !qubits_per_pass)) return -1;
+    const int np = (int)s->pass_q.size();
+    if (max < np) return -1;
+    for (int p = 0; p < np; ++p) qubits_per_pass[p] = s->pass_q[p];
+    return np;
+}
+
+qs_status qs_autotune_plan(qs_sim *s, int n_steps, int *qubits_per_pass, int max, int *n_passes,
+                           double *best_ms_per_step) {
+    qs_status st;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (n_steps < 1 || n_steps > 1000) FAIL(s, QS_ERR_ARG, "n_steps must be in [1, 1000]");
+    if (!qubits_per_pass || !n_passes || !best_ms_per_step) FAIL(s, QS_ERR_ARG, "null output");
+    if (s->n <= LT) FAIL(s, QS_ERR_ARG, "a pass plan needs more than %d qubits", LT);
+    const int r = s->n - LT, P = (r + 7) / 8;
+    if (max < P + 1) FAIL(s, QS_ERR_ARG, "qubits_per_pass needs %d entries", P + 1);
+    // every composition of r into P parts, each part in [lo, 8] (lo = 4 when possible)
+    const int lo = std::max(1, std::min(4, r / P));
+    std::vector<std::vector<int>> plans;
+    std::vector<int> cur;
+    std::function<void(int, int)> rec = [&](int left, int parts) {
+        if (parts == 0) { if (left == 0) plans.push_back(cur); return; }
+        for (int x = lo; x <= 8 && x <= left; ++x) {
+            cur.push_back(x);
+            rec(left - x, parts - 1);
+            cur.pop_back();
+        }
+    };
+    rec(r, P);
+    if (plans.empty()) FAIL(s, QS_ERR_STATE, "no pass plan");
+    const std::vector<int> saved_k = s->plan_k;
+    const long long saved_code = s->plan_code;
+    const int saved_method = s->method, saved_profile = s->profile, saved_graph = s->use_graph;
+    s->method = 0; s->profile = 0; s->use_graph = 0;
+    std::vector<qs_couplings> c(s->batch, qs_couplings{1.0, 1.0, 0.6, 0.6});
+    std::vector<double> sv(n_steps + 2);
+    for (int k = 0; k < n_steps + 2; ++k) sv[k] = (k + 0.5) / (n_steps + 2);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(s, cudaEventCreate(&e0));
+    CK(s, cudaEventCreate(&e1));
+    double best = 1e300;
+    size_t pick = 0;
+    for (size_t i = 0; i < plans.size() && st == QS_OK; ++i) {
+        s->plan_k = plans[i];
+        if ((st = rebuild_plan(s)) != QS_OK) break;
+        if ((st = qs_init_plus(s)) != QS_OK) break;
+        if ((st = qs_evolve(s, c.data(), sv.data(), 0.02, 2, 2)) != QS_OK) break;   // warm-up
+        if (cudaEventRecord(e0, s->stream) != cudaSuccess) { st = QS_ERR_CUDA; break; }
+        if ((st = qs_evolve(s, c.data(), sv.data() + 2, 0.02, n_steps, 2)) != QS_OK) break;
+        if (cudaEventRecord(e1, s->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            st = QS_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; pick = i; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->method = saved_method; s->profile = saved_profile; s->use_graph = saved_graph;
+    if (st != QS_OK) {
+        s->plan_k = saved_k;
+        s->plan_code = saved_code;
+        rebuild_plan(s);
+        return st;
+    }
+    s->plan_k = plans[pick];
+    s->plan_code = 0;
+    for (size_t j = 0; j < plans[pick].size(); ++j) s->plan_code |= (long long)plans[pick][j] << (4 * j);
+    if ((st = rebuild_plan(s)) != QS_OK) return st;
+    *n_passes = qs_plan(s, qubits_per_pass, max);
     *best_ms_per_step = best / n_steps;
     return QS_OK;
 }

@@ -24,7 +24,7 @@ QS_C64, QS_C128 = 0, 1
 QS_NOALLOC_MAX_BATCH = 16     # include/qsim.h
 QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
 QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_ADJOINT, \
-    QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL, QS_OPT_SHARED_BUFFERS = range(11)
+    QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL, QS_OPT_SHARED_BUFFERS, QS_OPT_PLAN = range(12)
 
 
 class QsError(RuntimeError):
@@ -80,6 +80,8 @@ _SIGS = {
     "qs_profile_read_kinds": ([_P, _DP, ctypes.POINTER(_LL)], _I),
     "qs_launch_count": ([_P], _LL),
     "qs_expect_z_noalloc": ([_P, _I, _I, _I, _U64, _P, _P], _I),
+    "qs_autotune_plan": ([_P, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _DP], _I),
+    "qs_plan": ([_P, ctypes.POINTER(_I), _I], _I),
 }
 
 
@@ -286,6 +288,31 @@ def qs_autotune(sim, n_steps: int = 20):
     return xp.value, nb.value, so.value, ns.value, ms.value
 
 
+def qs_autotune_plan(sim, n_steps: int = 20):
+    """Returns (qubits fused per pass, ms per step) of the fastest pass plan."""
+    buf = (_I * 16)()
+    np_, ms = _I(), ctypes.c_double()
+    _check(sim, library().qs_autotune_plan(sim, n_steps, buf, 16, ctypes.byref(np_), ctypes.byref(ms)))
+    return [buf[i] for i in range(np_.value)], ms.value
+
+
+def qs_plan(sim):
+    """Qubits fused by each tiled X pass (the first pass 12); [] below one tile."""
+    buf = (_I * 64)()
+    n = library().qs_plan(sim, buf, 64)
+    if n < 0:
+        raise QsError(1, "qs_plan failed")
+    return [buf[i] for i in range(n)]
+
+
+def plan_code(qubits_per_pass) -> int:
+    """QS_OPT_PLAN value of a plan given as qubits per pass (first pass 12)."""
+    code = 0
+    for j, k in enumerate(qubits_per_pass[1:]):
+        code |= int(k) << (4 * j)
+    return code
+
+
 def qs_selftest_wait(sim, limit_ms: float):
     _check(sim, library().qs_selftest_wait(sim, float(limit_ms)))
 
@@ -430,9 +457,10 @@ class Simulator:
         qs_sync(self.h)
 
     def autotune(self, n_steps: int = 20, cache: bool = True):
-        """Pick the fastest X-pass configuration for this lattice, dtype and batch on
-        this GPU, remembering it in a JSON cache (QSIM_CACHE, default
-        ~/.cache/qsim_gb300/autotune.json).  Overwrites the state."""
+        """Pick the fastest pass plan (qubits fused per X pass) and then the fastest
+        X-pass configuration for this lattice, dtype and batch on this GPU, remembering
+        both in a JSON cache (QSIM_CACHE, default ~/.cache/qsim_gb300/autotune.json).
+        Overwrites the state."""
         import json
         key = "|".join(str(x) for x in (self.torch.cuda.get_device_name(self.device), self.n, self.dtype_name,
                                         self.form, self.batch))
@@ -444,15 +472,19 @@ class Simulator:
                 table = json.load(open(path))
             except (OSError, ValueError):
                 table = {}
-        if cache and key in table and "shared_buffers" in table[key]:
+        if cache and key in table and "shared_buffers" in table[key] and "plan" in table[key]:
             e = table[key]
+            if self.n > 12:
+                self.set_option(QS_OPT_PLAN, plan_code(e["plan"]))
             self.set_option(QS_OPT_XPASS, e["xpass"])
             self.set_option(QS_OPT_TMA_BUFFERS, e["buffers"])
             self.set_option(QS_OPT_TMA_STORE, e["store"])
             self.set_option(QS_OPT_SHARED_BUFFERS, e["shared_buffers"])
             return e
+        plan, plan_ms = (qs_autotune_plan(self.h, n_steps) if self.n > 12 else (qs_plan(self.h), None))
         xp, nb, so, ns, ms = qs_autotune(self.h, n_steps)
-        entry = {"xpass": xp, "buffers": nb, "store": so, "shared_buffers": ns, "ms_per_step": ms}
+        entry = {"plan": plan, "plan_ms_per_step": plan_ms, "xpass": xp, "buffers": nb, "store": so,
+                 "shared_buffers": ns, "ms_per_step": ms}
         if cache:
             table[key] = entry
             try:
@@ -461,6 +493,9 @@ class Simulator:
             except OSError:
                 pass
         return entry
+
+    def plan(self):
+        return qs_plan(self.h)
 
     def dos(self):
         return qs_dos(self.h, self.batch)
