@@ -91,9 +91,13 @@ typedef enum {
     QS_OPT_TMA_BUFFERS = 5,   /* shared-memory tile buffers per CTA of the TMA kernel:
                                  2 (three CTAs per SM) or 3 (default; two CTAs per SM) */
     QS_OPT_ADJOINT = 6,       /* complex64 adjoint reverse pass: bit 0 set = register-
-                                 staged kernel, clear = TMA kernel (default); bit 1 set
-                                 = one tile buffer in the TMA kernel (two CTAs per SM),
-                                 clear = two buffers (default)                        */
+                                 staged kernel, clear = TMA kernel (default).  TMA
+                                 kernel, 0 (default): one psi/lambda tile-pair buffer
+                                 (two CTAs per SM), the next pair's load issued as soon
+                                 as the current pair's last stage is read, stores from
+                                 registers (tangent form); bit 1 set: two buffers (one
+                                 CTA per SM); bit 2 set: one buffer, load issued at the
+                                 start of each pair, bulk tensor stores              */
     QS_OPT_TMA_STORE = 7,     /* 1 (default): the TMA X pass writes each tile back with
                                  one bulk tensor store; 0: per-thread stores         */
     QS_OPT_XMERGE = 8,        /* 1 (default): complex64 runs on the TMA kernel share

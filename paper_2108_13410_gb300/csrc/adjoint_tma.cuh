@@ -138,7 +138,7 @@ __device__ __forceinline__ void adj_rotate(u64 (&p)[NR], u64 (&l)[NR], unsigned 
 // form the per-bit constants (t, -t), the 1 / (1 + t^2) factors and the per-stage scale
 // corrections of both rounds sit in a small shared-memory table (broadcast reads), which
 // keeps the kernel within 128 registers: two CTAs per SM with one tile-pair buffer each.
-template <int NBUF, bool TAN, bool MERGED>
+template <int NBUF, bool TAN, bool MERGED, bool EARLY>
 __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__restrict__ psi, float2 *__restrict__ lam,
                                                    const double *__restrict__ recs, int rec_stride, int tiles_shift,
                                                    int *__restrict__ err_flag, double *__restrict__ partials,
@@ -252,6 +252,26 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
         else adj_rotate_w(p, l, P.rot[st], cls, RC, g0, g1);
     };
 
+    // EARLY (one buffer): the next tile pair is loaded as soon as every thread has read the
+    // last stage of the current one from shared memory; both tiles then go back to HBM by
+    // per-thread stores from registers while the load is in flight
+    auto issue_next = [&](int it) {
+        if (EARLY) {
+            __syncthreads();
+            if (t == 0 && it + 1 < n_my) issue(it + 1);
+        }
+    };
+    long long toff_c = 0, toff_a = 0;   // EARLY: stage-C and stage-A global offsets of this thread
+    if (EARLY) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if ((tlo >> j) & 1) toff_c += P.toff_c[j];
+            if ((thi >> j) & 1) toff_c += P.toff_c[4 + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if ((t >> j) & 1) toff_a += P.toff_a[j];
+    }
     long long tile = first;
     for (int it = 0; it < n_my; ++it, tile += G) {
         const int b = it % NBUF;
@@ -295,7 +315,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
             cur_batch = batch;
             __syncthreads();
         }
-        if (NBUF == 1) {
+        if (NBUF == 1 && !(EARLY && it > 0)) {
             __syncthreads();                 // the single buffer is free again
             if (t == 0) issue(it);
         }
@@ -378,6 +398,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
         // ---- stage C ----
 #pragma unroll
         for (int r = 0; r < NR; ++r) { p[r] = tp[c_idx(r)]; l[r] = tl[c_idx(r)]; }
+        if (!MERGED) issue_next(it);
         unrot(0, 2, cls2, g0, g1, p, l);
         if (P.frame & 4) {
             const int k0 = -(__popc(tlo) + __popc(thi) + pc_tile);
@@ -430,17 +451,37 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
             }
 #pragma unroll
             for (int r = 0; r < NR; ++r) { p[r] = tp[a_base + (r << TB)]; l[r] = tl[a_base + (r << TB)]; }
+            issue_next(it);
             unrot(1, 0, cls0, g0b, g1b, p, l);
-            // back into the stage-A positions of the swizzled tiles
+            if (EARLY) {
+                const long long mid = tile & ((1ll << P.mid_bits) - 1), up = tile >> P.mid_bits;
+                const long long gbase = (mid << P.c) + (up << (P.next + P.k)) + toff_a;
+                u64 *dp = reinterpret_cast<u64 *>(psi + gbase);
+                u64 *dl = reinterpret_cast<u64 *>(lam + gbase);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) { tp[a_base + (r << TB)] = p[r]; tl[a_base + (r << TB)] = l[r]; }
+                for (int r = 0; r < NR; ++r) { dp[P.roff_a[r]] = p[r]; dl[P.roff_a[r]] = l[r]; }
+            } else {
+                // back into the stage-A positions of the swizzled tiles
+#pragma unroll
+                for (int r = 0; r < NR; ++r) { tp[a_base + (r << TB)] = p[r]; tl[a_base + (r << TB)] = l[r]; }
+            }
             add_tile(0, g0); add_tile(1, g1);
             add_tile(4, g0b); add_tile(5, g1b); add_tile(6, ga2); add_tile(7, gb2);
         } else {
+            if (EARLY) {
+                const long long mid = tile & ((1ll << P.mid_bits) - 1), up = tile >> P.mid_bits;
+                const long long gbase = (mid << P.c) + (up << (P.next + P.k)) + toff_c;
+                u64 *dp = reinterpret_cast<u64 *>(psi + gbase);
+                u64 *dl = reinterpret_cast<u64 *>(lam + gbase);
 #pragma unroll
-            for (int r = 0; r < NR; ++r) { tp[c_idx(r)] = p[r]; tl[c_idx(r)] = l[r]; }
+                for (int r = 0; r < NR; ++r) { dp[P.roff_c[r]] = p[r]; dl[P.roff_c[r]] = l[r]; }
+            } else {
+#pragma unroll
+                for (int r = 0; r < NR; ++r) { tp[c_idx(r)] = p[r]; tl[c_idx(r)] = l[r]; }
+            }
             add_tile(0, g0); add_tile(1, g1); add_tile(2, ga); add_tile(3, gb);
         }
+        if (EARLY) continue;
         // both tiles back to HBM by bulk tensor stores (same maps and boxes as the loads)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();

@@ -89,7 +89,7 @@ struct qs_sim {
     // persistent TMA X pass (complex64)
     int xpass_impl = 0;                    // 0 auto, 1 register kernel, 2 TMA kernel
     int nbuf = 3;                          // TMA shared-memory buffers per CTA (2 or 3)
-    int adj_nbuf = 2;                      // tile buffers of the TMA adjoint pass (1 or 2)
+    int adj_nbuf = 1;                      // tile-pair buffers of the TMA adjoint pass (1 or 2)
     int tma_store = 1;                     // X pass writes tiles back with TMA stores
     int xmerge = 1;                        // share the pass of one qubit group between factor groups
     int pdl = 1;                           // X passes launched with programmatic stream serialisation
@@ -98,6 +98,7 @@ struct qs_sim {
     int nX0 = 0, nX1 = 0;                  // X qubits per class
     bool tan_active = false;               // this call's X passes use the tangent form
     int adj_impl = 0;                      // adjoint reverse pass: 0 auto (TMA), 1 register kernel
+    int adj_early = 1;                     // one buffer, tangent form: next load issued before the stores
     int sm_count = 0;
     std::vector<TmaPass> tpasses;          // [NVAR * pass + variant]
     std::vector<CUtensorMap> tmaps;        // one per pass, encoded for the bound state
@@ -474,10 +475,14 @@ typedef void (*AdjKernel)(float2 *, float2 *, const double *, int, int, int *, d
 
 // k_adj_tma instantiation for (tile buffers, tangent form, shared reverse pass); shared
 // reverse passes exist in the tangent form only
-AdjKernel adj_tma_kernel(int nbuf, bool tan, bool merged = false) {
-    if (nbuf == 1) return tan ? (merged ? k_adj_tma<1, true, true> : k_adj_tma<1, true, false>)
-                              : k_adj_tma<1, false, false>;
-    return tan ? (merged ? k_adj_tma<2, true, true> : k_adj_tma<2, true, false>) : k_adj_tma<2, false, false>;
+AdjKernel adj_tma_kernel(int nbuf, bool tan, bool merged = false, bool early = false) {
+    if (nbuf == 1) {
+        if (early && tan) return merged ? k_adj_tma<1, true, true, true> : k_adj_tma<1, true, false, true>;
+        return tan ? (merged ? k_adj_tma<1, true, true, false> : k_adj_tma<1, true, false, false>)
+                   : k_adj_tma<1, false, false, false>;
+    }
+    return tan ? (merged ? k_adj_tma<2, true, true, false> : k_adj_tma<2, true, false, false>)
+               : k_adj_tma<2, false, false, false>;
 }
 
 // One X pass.  rec2 != nullptr selects the merged TMA pass: X of the pass's qubits from
@@ -1048,15 +1053,16 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
     // ---- reverse sweep ----
     const size_t nblk = (size_t)np * G;
     const bool use_tma = sizeof(R) == 4 && s->tmaps_ok && s->tmaps_aux_ok && s->adj_impl != 1;
-    const size_t adj_smem = 2 * (size_t)TMA_TILE_BYTES * s->adj_nbuf + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8;
     unsigned Gt = 1;
     // tangent form in the reverse sweep whenever the forward of this call used it (same
     // factor groups, so the same angle checks hold)
     const bool adj_tan = use_tma && s->tan_active;
-    const AdjKernel adj_kern = adj_tma_kernel(s->adj_nbuf, adj_tan);
+    const int adj_threads = NT;
+    const size_t adj_smem = 2 * (size_t)TMA_TILE_BYTES * s->adj_nbuf + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8;
+    const AdjKernel adj_kern = adj_tma_kernel(s->adj_nbuf, adj_tan, false, s->adj_early != 0);
     if (use_tma) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_kern, NT, adj_smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_kern, adj_threads, adj_smem);
         if (per_sm < 1) per_sm = 1;
         Gt = (unsigned)std::min<long long>((long long)B << (s->n - LT), (long long)per_sm * s->sm_count);
     }
@@ -1069,7 +1075,7 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
     // shared reverse passes: consecutive factor groups meet on one qubit group, as in the
     // forward sweep (orders ga, 0 .. np-3, gb and gb, 0 .. np-3, ga; ga = np-2, gb = np-1)
     const bool share = adj_tan && s->xmerge && np >= 2;
-    const AdjKernel adj_kern_m = adj_tma_kernel(s->adj_nbuf, true, true);
+    const AdjKernel adj_kern_m = adj_tma_kernel(s->adj_nbuf, true, true, s->adj_early != 0);
     int ord[2][64];
     for (int i = 0; i < np; ++i) {
         ord[0][i] = i == 0 ? np - 2 : (i == np - 1 ? np - 1 : i - 1);
@@ -1123,13 +1129,13 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
                     }
                     carry_done[0] = d2[0];
                     carry_done[1] = d2[1];
-                    adj_kern_m<<<Gt, NT, adj_smem, s->stream>>>(
+                    adj_kern_m<<<Gt, adj_threads, adj_smem, s->stream>>>(
                         (float2 *)s->state[0], (float2 *)s->state[1], rec, s->rec_stride, s->n - LT, s->d_err, part_j,
                         (int)nblk_t, i * (int)Gt, 0, rec_prev, part_prev, 0, s->tmaps[p], s->tmaps_aux[p], P);
                     next_carried = true;
                     dir ^= 1;
                 } else {
-                    adj_kern<<<Gt, NT, adj_smem, s->stream>>>(
+                    adj_kern<<<Gt, adj_threads, adj_smem, s->stream>>>(
                         (float2 *)s->state[0], (float2 *)s->state[1], rec, s->rec_stride, s->n - LT, s->d_err, part_j,
                         (int)nblk_t, i * (int)Gt, zinv, rec, part_j, 0, s->tmaps[p], s->tmaps_aux[p], P);
                 }
@@ -1289,9 +1295,11 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
             const bool tn = v >= 1, mg = v == 2;
             cudaFuncSetAttribute(adj_tma_kernel(2, tn, mg), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(4 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
-            cudaFuncSetAttribute(adj_tma_kernel(1, tn, mg), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(2 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
+            for (int ea = 0; ea < 2; ++ea)
+                cudaFuncSetAttribute(adj_tma_kernel(1, tn, mg, ea != 0), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(2 * TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
         }
+
     }
     size_t smem64 = (size_t)(1 << LT) * 16 + (size_t)s->max_lut * 16;
     cudaFuncSetAttribute(k_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem64);
@@ -1380,9 +1388,10 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
                 FAIL(s, QS_ERR_ARG, "shared-pass TMA buffers must be 0 (by form), 2 or 3");
             s->nbuf_shared = (int)value; return QS_OK;
         case QS_OPT_ADJOINT:
-            if (value < 0 || value > 3) FAIL(s, QS_ERR_ARG, "adjoint option must be 0..3");
+            if (value < 0 || value > 7) FAIL(s, QS_ERR_ARG, "adjoint option must be 0..7");
             s->adj_impl = (value & 1) ? 1 : 0;
-            s->adj_nbuf = (value & 2) ? 1 : 2;
+            s->adj_nbuf = (value & 2) ? 2 : 1;
+            s->adj_early = (value & 6) ? 0 : 1;
             return QS_OK;
         case QS_OPT_TMA_BUFFERS:
             if (value != 2 && value != 3) FAIL(s, QS_ERR_ARG, "TMA buffers must be 2 or 3");

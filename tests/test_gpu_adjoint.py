@@ -141,12 +141,14 @@ def test_batched_complex64_adjoint_tma_path(L):
 
 @gpu
 @pytest.mark.parametrize("T,n", [(2.0, 16), (8.0, 8)])
-@pytest.mark.parametrize("adj", [0, 2])
+@pytest.mark.parametrize("adj", [0, 2, 4])
 @pytest.mark.parametrize("merge", [1, 0])
 def test_complex64_adjoint_forms_and_buffers(T, n, adj, merge):
     """complex64 adjoint on the 3x2 torus in both forms of the reverse pass: small angles
     (T = 2, 16 steps) run the tangent form, large angles (T = 8, 8 steps: X angles
-    near 1) the (u, s) rotations; with two and one tile buffers (QS_OPT_ADJOINT 0, 2).
+    near 1) the (u, s) rotations; one tile-pair buffer with the next load issued before
+    the per-thread stores (QS_OPT_ADJOINT 0), two buffers (2), one buffer with bulk
+    tensor stores (4).
     Gradient within 1e-3 of the largest oracle component, value within 1e-4 relative,
     psi uncomputed back to |+> within 1e-4.  With shared passes (QS_OPT_XMERGE 1) the
     tangent-form reverse sweep shares one pass between consecutive factor groups."""
