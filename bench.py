@@ -431,41 +431,60 @@ def accuracy_leg(local, dev, n_steps=1000):
     return out
 
 
-def scan_leg(local, dev, chunk=64):
-    """Phase-diagram scan: 1024 (g, lambda) points on a 32 x 32 grid of [0, 1.5]^2,
-    even flat index -> 2x2 periodic gauge-Higgs (12 qubits, one persistent launch),
-    odd -> 3x2 open unitary gauge (17 qubits, batched chunks); complex64, linear
-    ramp T = 10, 200 second-order steps."""
+def scan_leg(local, dev, slots=304, baseline_points=4):
+    """Phase-diagram scan: 1024 (g, lambda) points on a 32 x 32 grid of [0, 1.5]^2, even flat
+    index -> 2x2 periodic gauge-Higgs (12 qubits), odd -> 3x2 open unitary gauge (17
+    qubits), all in one persistent launch (qs_scan_mixed: a 12-qubit point on chip, a
+    17-qubit point on its CTA's scratch slot), replayed as a CUDA graph; complex64, linear
+    ramp T = 10, 200 second-order steps.  Reported next to the same points run one at a
+    time through qs_evolve and the observables (per-point launches, a few points timed)."""
     import torch
     import synth
-    from paper_2108_13410_gb300 import Simulator
+    from paper_2108_13410_gb300 import Simulator, QS_OPT_GRAPH, QS_ENERGY
+    from paper_2108_13410_gb300.qsim import qs_scan_mixed
     grid = synth.coupling_grid(32, 0.0, 1.5)
     pts = [tuple(p) for p in grid]
     even, odd = pts[0::2], pts[1::2]
     T, n = 10.0, 200
     s = linear_midpoints(T, n)
-    out = {"points": len(pts), "steps": n, "T": T}
-    from paper_2108_13410_gb300 import QS_OPT_GRAPH
+    out = {"points": len(pts), "steps": n, "T": T, "launches": 1, "graph": True}
     sim12 = Simulator(2, 2, form="gh", dtype="c64", device=f"cuda:{local}")
-    sim12.set_option(QS_OPT_GRAPH, 1)                          # copy-in, launch, copy-out as one graph
-    sim12.scan(even, s, T / n, 2)                              # warm-up (captures the graph)
+    sim17 = Simulator(3, 2, form="ug", dtype="c64", boundary="open", batch=slots, device=f"cuda:{local}")
+    sim17.set_option(QS_OPT_GRAPH, 1)
+    qs_scan_mixed(sim12.h, even, sim17.h, odd, s, T / n, 2)          # warm-up (captures the graph)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    r12 = sim12.scan(even, s, T / n, 2)
-    t12 = time.perf_counter() - t0
-    sim17 = Simulator(3, 2, form="ug", dtype="c64", boundary="open", batch=chunk, device=f"cuda:{local}")
-    sim17.scan(odd[:chunk], s[:5], T / n, 2)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    r17 = sim17.scan(odd, s, T / n, 2)
-    t17 = time.perf_counter() - t0
-    out["gh2x2_12q"] = {"points": len(even), "seconds": t12, "point_steps_per_s": len(even) * n / t12,
-                        "launches": 1, "graph": True,
-                        "energy_range": [float(r12[:, 0].min()), float(r12[:, 0].max())]}
-    out["ug3x2open_17q"] = {"points": len(odd), "seconds": t17, "point_steps_per_s": len(odd) * n / t17,
-                            "chunk": chunk, "energy_range": [float(r17[:, 0].min()), float(r17[:, 0].max())]}
-    out["seconds"] = t12 + t17
-    out["point_steps_per_s"] = len(pts) * n / (t12 + t17)
+    r12, r17 = qs_scan_mixed(sim12.h, even, sim17.h, odd, s, T / n, 2)
+    sec = time.perf_counter() - t0
+    state17 = 8 << 17
+    out.update({"seconds": sec, "point_steps_per_s": len(pts) * n / sec,
+                "amplitude_updates_per_s": (len(even) * 4096 + len(odd) * (1 << 17)) * n / sec,
+                "scratch_slots": slots,
+                # 17-qubit points: two Walsh-Hadamard passes per factor group, each a read
+                # and a write of the 1 MiB state (L2-resident slots)
+                "state_traffic_gbs_17q": len(odd) * (n + 1) * 2 * 2 * state17 / sec / 1e9,
+                "energy_range_12q": [float(r12[:, 0].min()), float(r12[:, 0].max())],
+                "energy_range_17q": [float(r17[:, 0].min()), float(r17[:, 0].max())]})
+    # per-point launches: each point through qs_evolve (one launch per pass) and the energy
+    base = {}
+    for name, sim, plist in (("gh2x2_12q", Simulator(2, 2, form="gh", dtype="c64", device=f"cuda:{local}"), even),
+                             ("ug3x2open_17q", Simulator(3, 2, form="ug", dtype="c64", boundary="open",
+                                                         device=f"cuda:{local}"), odd)):
+        sim.init_plus()
+        sim.evolve([plist[0]], s[:3], T / n, 2)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for p in plist[:baseline_points]:
+            sim.init_plus()
+            sim.evolve([p], s, T / n, 2)
+            sim.expect(QS_ENERGY, 0, [p], 1.0)
+        el = time.perf_counter() - t0
+        base[name] = {"points_timed": baseline_points, "seconds_per_point": el / baseline_points,
+                      "point_steps_per_s": baseline_points * n / el}
+        del sim
+    out["per_point_launches"] = base
+    out["speedup_vs_per_point_launches"] = (out["point_steps_per_s"] / (len(pts) * n / (
+        len(even) * base["gh2x2_12q"]["seconds_per_point"] + len(odd) * base["ug3x2open_17q"]["seconds_per_point"])))
     del sim12, sim17
     torch.cuda.empty_cache()
     return out

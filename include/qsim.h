@@ -119,7 +119,7 @@ typedef enum {
                                  per SM) or 0 (default): 2 for tangent-form rotations
                                  (gauge-Higgs), 3 for Walsh-Hadamard passes (unitary
                                  gauge), the faster of the two for each as measured */
-    QS_OPT_PLAN = 11          /* pass plan of the tiled X layer: how many new qubits
+    QS_OPT_PLAN = 11,         /* pass plan of the tiled X layer: how many new qubits
                                  each pass after the first fuses (the first pass always
                                  takes qubits 0..11).  Value: one 4-bit field per pass,
                                  lowest first, each in [1, 8], summing to n - 12 (a pass
@@ -127,6 +127,11 @@ typedef enum {
                                  low qubits, 2^(12-k) amplitudes per row); 0 (default):
                                  8 per pass, the remainder last.  Rejected (QS_ERR_ARG)
                                  for states of fewer than 13 qubits.                  */
+    QS_OPT_SCAN_BUFFERS = 12  /* qs_scan_mixed: 32 KB tile buffers per CTA of the
+                                 larger lattice's passes, 2 or 3 (two CTAs per SM) or 4
+                                 or 6 (one CTA per SM; a pass keeps buffers - 1 loads in
+                                 flight); 0: the default, 3 (with one scratch slot
+                                 per CTA, 2 x SMs slots, measured fastest)            */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open
@@ -244,6 +249,26 @@ qs_status qs_dos(qs_sim *sim, double *out);
  * Outputs the choice and its ms per step (host). */
 qs_status qs_autotune(qs_sim *sim, int n_steps, int *best_xpass, int *best_buffers, int *best_store,
                       int *best_shared_buffers, double *best_ms_per_step);
+
+/* Phase-diagram scan of two lattices in one persistent launch (Sec. V: the phase diagram
+ * is mapped by independent adiabatic runs, Sec. III, at many coupling points).  sim12: a
+ * 12-qubit gauge-Higgs lattice (the 2x2 torus), complex64; sim: an open unitary-gauge
+ * lattice of 13..20 qubits (the 3x2 open lattice has 17), complex64, whose bound state
+ * (slot 0, `batch` states) is the scratch: one state slot per CTA, so at most `batch`
+ * CTAs run.  For each of the n12 points p12[i] (sim12's lattice) and n17 points p17[i]
+ * (sim's lattice): |+>^n evolved over the schedule s[0 .. n_steps-1] (step midpoints),
+ * time step dt, Trotter order 1 or 2, then the observables of qs_scan into out12[i * 8 +
+ * k] and out17[i * 8 + k] (host; energy <H1>, mean <B_p>, W_x, W_y, norm, mean <X> on
+ * links, mean <X> on vertices, 0).  CTAs take points from a work queue; a 12-qubit point
+ * runs in shared memory, a larger one on the CTA's scratch slot as two TMA-pipelined
+ * Walsh-Hadamard passes per Trotter factor group.  The bound state is overwritten.  With
+ * QS_OPT_GRAPH set on sim the copies and the launch are captured once per shape as a CUDA
+ * graph and replayed.  Stream-ordered on sim's stream, synchronises it.  Errors:
+ * QS_ERR_ARG (lattices, dtypes, counts, null pointers), QS_ERR_STATE (no bound state),
+ * QS_ERR_TIMEOUT (a bounded wait gave up), QS_ERR_CUDA. */
+qs_status qs_scan_mixed(qs_sim *sim12, const qs_couplings *p12, int n12, qs_sim *sim, const qs_couplings *p17,
+                        int n17, const double *s, double dt, int n_steps, int order, double *out12,
+                        double *out17);
 
 /* Pass-plan autotuner (the fusion width of the tiled X layer): times n_steps
  * second-order steps with every plan of the fewest passes whose passes each fuse 4 to 8

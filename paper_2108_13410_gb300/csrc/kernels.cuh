@@ -530,6 +530,37 @@ __device__ inline void dev_unit_pair(bool f32, double t, double *ou, double *os)
     *ou = bu; *os = bs;
 }
 
+// Careful pair of exp(i t) = (1 - u) + i s for per-step tables built inside a kernel:
+// one FP64 sincos, then a 3 x 3 search over the float neighbours of s and of the u that
+// makes (1 - u)^2 + s^2 = 1 for each of them, keeping the pair with the smallest
+// |(1 - u)^2 + s^2 - 1| (evaluated in FP64).  complex128 tables take (u, s) as they are.
+// About a tenth of dev_unit_pair's FP64 work, which matters where a table is rebuilt
+// for every Trotter step inside a persistent kernel (GB300 retires about two FP64 FMAs
+// per clock per SM).
+template <typename R>
+__device__ inline void dev_unit_pair_fast(double t, R *ou, R *os) {
+    double sh, ch;
+    sincos(0.5 * t, &sh, &ch);
+    const double u = 2.0 * sh * sh, s = 2.0 * sh * ch;
+    if (sizeof(R) == 8) { *ou = (R)u; *os = (R)s; return; }
+    const bool neg = u > 1.0;           // cos t < 0: 1 - u = -sqrt(1 - s^2)
+    float bu = (float)u, bs = (float)s;
+    double be = 1e300;
+    float sc = nextafterf((float)s, -4.0f);
+    for (int i = 0; i < 3; ++i, sc = nextafterf(sc, 4.0f)) {
+        const double s2 = (double)sc * (double)sc;
+        const double r = sqrt(fmax(0.0, 1.0 - s2));
+        const double us = neg ? 1.0 + r : s2 / (1.0 + r);
+        float uc = nextafterf((float)us, -4.0f);
+        for (int j = 0; j < 3; ++j, uc = nextafterf(uc, 4.0f)) {
+            const double c = 1.0 - (double)uc;
+            const double e = fabs(c * c + s2 - 1.0);
+            if (e < be) { be = e; bu = uc; bs = sc; }
+        }
+    }
+    *ou = (R)bu; *os = (R)bs;
+}
+
 // X angles and Z angles of factor group `op` for couplings c:
 //   order 1:      op k (< N): X theta(s_k) dt, Z at s_k
 //   second order: op k (<= N): X theta(s_k) dt/2 [k < N] + theta(s_{k-1}) dt/2 [k > 0],

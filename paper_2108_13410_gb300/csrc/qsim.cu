@@ -22,6 +22,7 @@
 #include "adjoint.cuh"
 #include "adjoint_tma.cuh"
 #include "scan.cuh"
+#include "scan_mixed.cuh"
 
 using namespace qsim;
 
@@ -123,6 +124,8 @@ struct qs_sim {
     bool in_path = false; size_t in_ncpl = 0;
     // scan workspaces
     double *d_scan = nullptr; size_t scan_cap = 0;
+    int *d_queue = nullptr;                // work-queue counter of the mixed scan
+    int scan_buffers = 3;                  // tile buffers of the mixed scan's 17-qubit passes
     double *h_scan = nullptr; size_t h_scan_cap = 0;
 };
 
@@ -1185,6 +1188,24 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
     return QS_OK;
 }
 
+// Parameters of the on-chip 12-qubit scan (the 2x2 torus in the gauge-Higgs form).
+ScanParams scan12_params(const qs_sim *s, int n_points, int n_steps, int order, double dt) {
+    ScanParams P;
+    memset(&P, 0, sizeof(P));
+    P.n_points = n_points; P.n_ops = order == 2 ? n_steps + 1 : n_steps;
+    P.G.n_steps = n_steps; P.G.order = order; P.G.fsal = order == 2; P.G.batch = 1; P.G.dt = dt;
+    P.G.f32 = s->dtype == QS_C64;
+    P.nA = s->nA; P.nB = s->nB;
+    for (int q = 0; q < LT; ++q) {
+        for (int k = 0; k < s->nA; ++k) if ((s->lat.plaquettes[k] >> q) & 1) P.colA[q] |= 1u << k;
+        for (int k = 0; k < s->nB; ++k) if ((s->lat.second[k] >> q) & 1) P.colB[q] |= 1u << k;
+        if (s->lat.x_class[q]) P.cls_mask |= 1u << q;
+    }
+    if (s->lat.wilson.size() == 2) { P.wx = (uint32_t)s->lat.wilson[0]; P.wy = (uint32_t)s->lat.wilson[1]; }
+    P.n_link = s->lat.n_links; P.n_vertex = s->n - s->lat.n_links;
+    return P;
+}
+
 qs_status check_ready(qs_sim *s) {
     if (!s) return QS_ERR_ARG;
     if (!s->state[0]) FAIL(s, QS_ERR_STATE, "no state bound (qs_bind_state slot 0)");
@@ -1322,6 +1343,7 @@ void qs_destroy(qs_sim *s) {
     cudaFree(s->d_grad);
     cudaFree(s->d_hrec);
     cudaFree(s->d_scan);
+    cudaFree(s->d_queue);
     cudaFree(s->d_in);
     if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
     if (s->scan_graph) cudaGraphExecDestroy(s->scan_graph);
@@ -1396,6 +1418,11 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
         case QS_OPT_TMA_BUFFERS:
             if (value != 2 && value != 3) FAIL(s, QS_ERR_ARG, "TMA buffers must be 2 or 3");
             s->nbuf = (int)value; return QS_OK;
+        case QS_OPT_SCAN_BUFFERS:
+            if (value != 0 && value != 2 && value != 3 && value != 4 && value != 6)
+                FAIL(s, QS_ERR_ARG, "scan tile buffers must be 0 (default 3), 2, 3, 4 or 6");
+            s->scan_buffers = value ? (int)value : 3;
+            return QS_OK;
         case QS_OPT_PLAN: {
             if (s->n <= LT) FAIL(s, QS_ERR_ARG, "a pass plan needs more than %d qubits", LT);
             if (value < 0) FAIL(s, QS_ERR_ARG, "bad plan");
@@ -1668,7 +1695,7 @@ qs_status qs_scan(qs_sim *s, const qs_couplings *points, int n_points, const dou
     if (n_points < 1 || n_steps < 1) FAIL(s, QS_ERR_ARG, "n_points and n_steps must be >= 1");
     if (order != 1 && order != 2) FAIL(s, QS_ERR_ARG, "order must be 1 or 2");
     const int nops = order == 2 ? n_steps + 1 : n_steps;
-    if (s->n == LT && s->lat.gauge_higgs && (s->nA + 1) * (s->nB + 1) <= 64) {
+    if (s->n == LT && s->lat.gauge_higgs && s->nA + s->nB + 2 <= 64) {
         // ---- every point in one persistent launch, state in shared memory ----
         size_t in_doubles = (size_t)n_points * 4 + (size_t)n_steps;
         size_t out_doubles = (size_t)n_points * SCAN_NOBS;
@@ -1680,19 +1707,7 @@ qs_status qs_scan(qs_sim *s, const qs_couplings *points, int n_points, const dou
             s->h_scan[4 * p + 2] = points[p].g; s->h_scan[4 * p + 3] = points[p].lambda;
         }
         memcpy(s->h_scan + 4 * (size_t)n_points, sv, (size_t)n_steps * sizeof(double));
-        ScanParams P;
-        memset(&P, 0, sizeof(P));
-        P.n_points = n_points; P.n_ops = nops;
-        P.G.n_steps = n_steps; P.G.order = order; P.G.fsal = order == 2; P.G.batch = 1; P.G.dt = dt;
-        P.G.f32 = s->dtype == QS_C64;
-        P.nA = s->nA; P.nB = s->nB;
-        for (int q = 0; q < LT; ++q) {
-            for (int k = 0; k < s->nA; ++k) if ((s->lat.plaquettes[k] >> q) & 1) P.colA[q] |= 1u << k;
-            for (int k = 0; k < s->nB; ++k) if ((s->lat.second[k] >> q) & 1) P.colB[q] |= 1u << k;
-            if (s->lat.x_class[q]) P.cls_mask |= 1u << q;
-        }
-        if (s->lat.wilson.size() == 2) { P.wx = (uint32_t)s->lat.wilson[0]; P.wy = (uint32_t)s->lat.wilson[1]; }
-        P.n_link = s->lat.n_links; P.n_vertex = s->n - s->lat.n_links;
+        const ScanParams P = scan12_params(s, n_points, n_steps, order, dt);
         int per_sm = 0;
         if (s->dtype == QS_C64) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan12<float>, NT, 0);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan12<double>, NT, 0);
@@ -1817,6 +1832,110 @@ qs_status qs_dos(qs_sim *s, double *out) {
     for (int i = 0; i < B * nbins; ++i)
         if (!std::isfinite(out[i])) FAIL(s, QS_ERR_NONFINITE, "non-finite density of states");
     return check_device_flag(s);
+}
+
+qs_status qs_scan_mixed(qs_sim *s12, const qs_couplings *p12, int n12, qs_sim *s, const qs_couplings *p17,
+                        int n17, const double *sv, double dt, int n_steps, int order, double *out12, double *out17) {
+    qs_status st;
+    if (!s) return QS_ERR_ARG;
+    if ((st = check_ready(s)) != QS_OK) return st;
+    if (n12 < 0 || n17 < 0 || n12 + n17 < 1) FAIL(s, QS_ERR_ARG, "need at least one point");
+    if (n_steps < 1) FAIL(s, QS_ERR_ARG, "n_steps must be >= 1");
+    if (order != 1 && order != 2) FAIL(s, QS_ERR_ARG, "order must be 1 or 2");
+    if (!sv || (n17 > 0 && (!p17 || !out17)) || (n12 > 0 && (!p12 || !out12 || !s12)))
+        FAIL(s, QS_ERR_ARG, "null argument");
+    if (s->lat.gauge_higgs || s->boundary != QS_OPEN || s->n <= LT || s->n > LT + 8 || s->dtype != QS_C64)
+        FAIL(s, QS_ERR_ARG, "the mixed scan's second simulator must be an open unitary-gauge lattice of 13..20 "
+                            "qubits in complex64");
+    if (!s->tmaps_ok || s->passes.size() != 2) FAIL(s, QS_ERR_STATE, "no TMA pass plan over the bound state");
+    if (n12 > 0 && (s12->n != LT || !s12->lat.gauge_higgs || s12->dtype != QS_C64 || s12->nA + s12->nB + 2 > 64))
+        FAIL(s, QS_ERR_ARG, "the mixed scan's first simulator must be a 12-qubit gauge-Higgs lattice in complex64");
+    const int nops = order == 2 ? n_steps + 1 : n_steps;
+    const size_t in_doubles = 4 * (size_t)(n12 + n17) + (size_t)n_steps;
+    const size_t out_doubles = (size_t)(n12 + n17) * SCAN_NOBS;
+    if ((st = grow(s, &s->d_scan, &s->scan_cap, in_doubles + out_doubles, false)) != QS_OK) return st;
+    if ((st = grow(s, &s->h_scan, &s->h_scan_cap, in_doubles + out_doubles, true)) != QS_OK) return st;
+    if (!s->d_queue) CK(s, cudaMalloc((void **)&s->d_queue, sizeof(int)));
+    auto put = [&](const qs_couplings *p, int n, double *dst) {
+        for (int i = 0; i < n; ++i) {
+            dst[4 * i] = p[i].J; dst[4 * i + 1] = p[i].h; dst[4 * i + 2] = p[i].g; dst[4 * i + 3] = p[i].lambda;
+        }
+    };
+    put(p12, n12, s->h_scan);
+    put(p17, n17, s->h_scan + 4 * (size_t)n12);
+    memcpy(s->h_scan + 4 * (size_t)(n12 + n17), sv, (size_t)n_steps * sizeof(double));
+    ScanParams P12;
+    memset(&P12, 0, sizeof(P12));
+    if (n12 > 0) P12 = scan12_params(s12, n12, n_steps, order, dt);
+    P12.n_points = n12;
+    ScanUGParams U;
+    memset(&U, 0, sizeof(U));
+    U.n_points = n17; U.n_ops = nops;
+    U.G.n_steps = n_steps; U.G.order = order; U.G.fsal = order == 2; U.G.batch = 1; U.G.dt = dt; U.G.f32 = 1;
+    U.n = s->n; U.nP = s->nA; U.nL = s->nB; U.nS = s->nXA;
+    U.tiles_shift = s->n - LT;
+    U.scale = (float)ldexp(1.0, -s->n);
+    U.p0 = s->tpasses[NVAR * 0 + V_HAD_Z];
+    U.p1 = s->tpasses[NVAR * 1 + V_HAD_X];
+    // tile buffers of the 17-qubit passes: 2 or 3 (two CTAs per SM; 3, the default, measured
+    // fastest with 2 x SMs scratch slots) or 4 or 6 (one CTA per SM)
+    const int nb = s->scan_buffers;
+    typedef void (*MixKernel)(const DevCouplings *, const DevCouplings *, const double *, double *, double *, int *,
+                              int *, const CUtensorMap, const CUtensorMap, const ScanParams, const ScanUGParams);
+    const MixKernel kern = nb == 2 ? k_scan_mixed<2> : nb == 3 ? k_scan_mixed<3> : nb == 4 ? k_scan_mixed<4>
+                                                                                              : k_scan_mixed<6>;
+    const size_t smem = (size_t)nb * TMA_TILE_BYTES + 1024;
+    CK(s, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+    if (per_sm < 1) per_sm = 1;
+    long long g = std::min<long long>((long long)per_sm * s->sm_count, n12 + n17);
+    if (n17 > 0) g = std::min<long long>(g, s->batch);   // one scratch slot per CTA
+    const unsigned grid = (unsigned)g;
+    const DevCouplings *c12 = reinterpret_cast<const DevCouplings *>(s->d_scan);
+    const DevCouplings *c17 = c12 + n12;
+    const double *dsv = s->d_scan + 4 * (size_t)(n12 + n17);
+    double *dout12 = s->d_scan + in_doubles, *dout17 = dout12 + (size_t)n12 * SCAN_NOBS;
+    auto enqueue = [&](cudaStream_t q) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(s->d_scan, s->h_scan, in_doubles * sizeof(double), cudaMemcpyHostToDevice, q);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(s->d_queue, 0, sizeof(int), q)) != cudaSuccess) return e;
+        kern<<<grid, NT, smem, q>>>(c12, c17, dsv, dout12, dout17, s->d_queue, s->d_err, s->tmaps[0], s->tmaps[1],
+                                     P12, U);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return cudaMemcpyAsync(s->h_scan + in_doubles, dout12, out_doubles * sizeof(double), cudaMemcpyDeviceToHost,
+                               q);
+    };
+    if (s->use_graph) {
+        const long long key[10] = {-2 - 16 * nb, n12, n17, n_steps, order, (long long)(uintptr_t)s->d_scan,
+                                   (long long)(uintptr_t)s->h_scan, (long long)grid,
+                                   (long long)llround(dt * 1e15), (long long)(uintptr_t)s->state[0]};
+        if (!s->scan_graph || memcmp(key, s->scan_key, sizeof(key)) != 0) {
+            if (s->scan_graph) { cudaGraphExecDestroy(s->scan_graph); s->scan_graph = nullptr; }
+            if (!s->cap_stream) CK(s, cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+            CK(s, cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e1 = enqueue(s->cap_stream);
+            cudaGraph_t gr = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &gr);
+            if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                FAIL(s, QS_ERR_CUDA, "scan graph capture: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+            }
+            cudaError_t e3 = cudaGraphInstantiate(&s->scan_graph, gr, 0);
+            cudaGraphDestroy(gr);
+            if (e3 != cudaSuccess) { s->scan_graph = nullptr; FAIL(s, QS_ERR_CUDA, "scan graph: %s", cudaGetErrorString(e3)); }
+            memcpy(s->scan_key, key, sizeof(key));
+        }
+        CK(s, cudaGraphLaunch(s->scan_graph, s->stream));
+    } else {
+        CK(s, enqueue(s->stream));
+    }
+    s->launches++;
+    CK(s, cudaStreamSynchronize(s->stream));
+    if ((st = check_device_flag(s)) != QS_OK) return st;
+    if (n12 > 0) memcpy(out12, s->h_scan + in_doubles, (size_t)n12 * SCAN_NOBS * sizeof(double));
+    if (n17 > 0) memcpy(out17, s->h_scan + in_doubles + (size_t)n12 * SCAN_NOBS, (size_t)n17 * SCAN_NOBS * sizeof(double));
+    return QS_OK;
 }
 
 qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers, int *best_store,

@@ -24,7 +24,7 @@ QS_C64, QS_C128 = 0, 1
 QS_NOALLOC_MAX_BATCH = 16     # include/qsim.h
 QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
 QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_ADJOINT, \
-    QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL, QS_OPT_SHARED_BUFFERS, QS_OPT_PLAN = range(12)
+    QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL, QS_OPT_SHARED_BUFFERS, QS_OPT_PLAN, QS_OPT_SCAN_BUFFERS = range(13)
 
 
 class QsError(RuntimeError):
@@ -82,6 +82,7 @@ _SIGS = {
     "qs_expect_z_noalloc": ([_P, _I, _I, _I, _U64, _P, _P], _I),
     "qs_autotune_plan": ([_P, _I, ctypes.POINTER(_I), _I, ctypes.POINTER(_I), _DP], _I),
     "qs_plan": ([_P, ctypes.POINTER(_I), _I], _I),
+    "qs_scan_mixed": ([_P, _CP, _I, _P, _CP, _I, _DP, _D, _I, _I, _DP, _DP], _I),
 }
 
 
@@ -265,6 +266,19 @@ def qs_scan(sim, points, s: Sequence[float], dt: float, order: int = 2):
     _check(sim, library().qs_scan(sim, pts, len(points), sv.ctypes.data_as(_DP), dt, int(sv.size), order,
                                   out.ctypes.data_as(_DP)))
     return out
+
+
+def qs_scan_mixed(sim12, points12, sim, points17, s: Sequence[float], dt: float, order: int = 2):
+    """Both lattices' points in one launch; returns (out12[n12, 8], out17[n17, 8])."""
+    n12, n17 = len(points12), len(points17)
+    p12 = _couplings(points12, n12) if n12 else None
+    p17 = _couplings(points17, n17) if n17 else None
+    sv = np.ascontiguousarray(s, dtype=np.float64)
+    o12 = np.zeros((max(n12, 1), QS_SCAN_NOBS), dtype=np.float64)
+    o17 = np.zeros((max(n17, 1), QS_SCAN_NOBS), dtype=np.float64)
+    _check(sim, library().qs_scan_mixed(sim12, p12, n12, sim, p17, n17, sv.ctypes.data_as(_DP), dt, int(sv.size),
+                                        order, o12.ctypes.data_as(_DP), o17.ctypes.data_as(_DP)))
+    return o12[:n12], o17[:n17]
 
 
 def qs_num_links(sim) -> int:
