@@ -259,7 +259,12 @@ def run_ours(args):
     sim = Simulator(W["Lx"], W["Ly"], form=W["form"], dtype=W["dtype"], device=f"cuda:{local}")
     stream = torch.cuda.current_stream(dev)
     # autotuner: pass plan (qubits fused per X pass), then the X-pass kernel configuration
-    tune = sim.autotune(n_steps=20, cache=False)
+    if args.no_autotune:
+        from paper_2108_13410_gb300.qsim import qs_plan
+        tune = {"plan": qs_plan(sim.h), "xpass": 0, "buffers": 3, "store": 1, "shared_buffers": 0,
+                "ms_per_step": None}
+    else:
+        tune = sim.autotune(n_steps=20, cache=False)
     sim.init_plus()
     # warm-up
     sim.evolve(cpl, sched[:Wu], dt, W["order"])
@@ -625,6 +630,8 @@ def main():
     ap.add_argument("--no-pergate", action="store_true")
     ap.add_argument("--no-ug32", action="store_true", help="skip the 32-qubit unitary-gauge leg")
     ap.add_argument("--no-protocol", action="store_true", help="skip the hysteresis-protocol leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default X-pass configuration (fewer launches before the timed steps)")
     ap.add_argument("--source-hash", action="store_true", help="print the X-pass kernel source hash")
     args = ap.parse_args()
     if args.source_hash:
