@@ -1,8 +1,10 @@
 """Phase-diagram scan (qs_scan): every coupling point is an independent adiabatic
 run; the observables per point match the oracle's run of that point.
 
-Tolerances as in the parity tests: observables of norm <= 1 within 1e-6 (complex128)
-and 2e-5 (complex64); energies 1e-6 (complex128) and 2 ||H|| 1e-5 (complex64).
+Tolerances: observables of norm <= 1 within 1e-6 (complex128) and 3e-6 (complex64, about
+3x the largest error measured on these cases, 1.0e-6); energies 1e-6 (complex128) and
+1.2e-6 ||H|| (complex64, ||H|| <= the sum of |coefficients|; measured |dE| / ||H|| <= 3.5e-7,
+the ratio of the parity tests).
 """
 import numpy as np
 import pytest
@@ -26,8 +28,8 @@ def _oracle_obs(lat, c, s, dt, order):
 
 
 def _check(got, ref, dtype, hbound):
-    obs_tol = 1e-6 if dtype == "c128" else 2e-5
-    e_tol = 1e-6 if dtype == "c128" else 2 * hbound * 1e-5
+    obs_tol = 1e-6 if dtype == "c128" else 3e-6
+    e_tol = 1e-6 if dtype == "c128" else 1.2e-6 * hbound
     assert abs(got[0] - ref[0]) <= e_tol, (got[0], ref[0])
     np.testing.assert_allclose(got[1:], ref[1:], atol=obs_tol)
 
