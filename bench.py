@@ -56,11 +56,13 @@ def workload_config(world: int) -> dict:
             "parallelism": "replicas" if world > 1 else "single"}
 
 
-def kernel_source_hash() -> str:
-    """sha256 (16 hex digits) of the X-pass kernel sources."""
+def kernel_source_hash(kernel_name: str = "") -> str:
+    """sha256 (16 hex digits) of the X-pass kernel sources (the warp-local shared pass
+    adds its own header)."""
     import hashlib
     d = hashlib.sha256()
-    for f in ("kernels.cuh", "xpass_tma.cuh"):
+    files = ["kernels.cuh", "xpass_tma.cuh"] + (["xpass_wl.cuh"] if kernel_name.startswith("k_xpass_wl") else [])
+    for f in files:
         d.update(open(os.path.join(ROOT, "paper_2108_13410_gb300", "csrc", f), "rb").read())
     return d.hexdigest()[:16]
 
@@ -74,7 +76,7 @@ def profile_traffic(kernel_tag: str, kernel_name: str = ""):
         return None
     if kernel_name and not open(path).readline().startswith(kernel_name):
         return None
-    h = kernel_source_hash()
+    h = kernel_source_hash(kernel_name)
     vals = {}
     for line in open(path):
         if ":" in line:
@@ -262,7 +264,7 @@ def run_ours(args):
     if args.no_autotune:
         from paper_2108_13410_gb300.qsim import qs_plan
         tune = {"plan": qs_plan(sim.h), "xpass": 0, "buffers": 3, "store": 1, "shared_buffers": 0,
-                "ms_per_step": None}
+                "shared_kernel": 1, "ms_per_step": None}
     else:
         tune = sim.autotune(n_steps=20, cache=False)
     sim.init_plus()
@@ -300,9 +302,13 @@ def run_ours(args):
     tb = lambda v: "true" if v else "false"
     names = ("k_xpass_tma<%d, %s, false, true>" % (tune["buffers"], tb(tune["store"])),
              "k_xpass_tma<%d, %s, true, true>" % (tune["shared_buffers"] or 2, tb(tune["store"])))
+    tags = ("k_xpass_tma_c64_27q", "k_xpass_tma_shared_c64_27q")
+    if tune["shared_kernel"] == 1 and tune["store"]:  # warp-local shared passes
+        geom = {0: "6, 24, 1", 2: "2, 8, 3", 3: "3, 8, 2"}[tune["shared_buffers"]]
+        names = (names[0], "k_xpass_wl<%s>" % geom)
+        tags = (tags[0], "k_xpass_wl_c64_27q")
     if tune["xpass"] == 1:                            # the register-staged kernel (no shared passes)
         names = ("k_xpass<float>", "k_xpass<float>")
-    tags = ("k_xpass_tma_c64_27q", "k_xpass_tma_shared_c64_27q")
     dom = 0 if kinds[0][0] >= kinds[1][0] else 1     # dominant kernel: larger total time
     per_kind = {}
     for kd in (0, 1):
@@ -390,6 +396,7 @@ def run_ours(args):
                "tuning": {"plan_qubits_per_pass": tune["plan"], "xpass_kernel": tune["xpass"],
                           "tile_buffers": tune["buffers"], "bulk_store": tune["store"],
                           "shared_pass_buffers": tune["shared_buffers"],
+                          "shared_pass_kernel": "warp-local" if tune["shared_kernel"] == 1 else "cta-staged",
                           "tuned_ms_per_step": tune["ms_per_step"]}}
         out.update(extra)
         print(json.dumps(out))
@@ -632,10 +639,11 @@ def main():
     ap.add_argument("--no-protocol", action="store_true", help="skip the hysteresis-protocol leg")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default X-pass configuration (fewer launches before the timed steps)")
-    ap.add_argument("--source-hash", action="store_true", help="print the X-pass kernel source hash")
+    ap.add_argument("--source-hash", action="store_true",
+                    help="print the X-pass kernel source hashes (CTA-staged kernels, warp-local shared pass)")
     args = ap.parse_args()
     if args.source_hash:
-        print(kernel_source_hash())
+        print(kernel_source_hash(), kernel_source_hash("k_xpass_wl"))
         return 0
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -116,9 +116,12 @@ typedef enum {
                                  global memory; 0: plain stream order             */
     QS_OPT_SHARED_BUFFERS = 10, /* tile buffers per CTA of the shared X passes
                                  (QS_OPT_XMERGE): 2 (three CTAs per SM), 3 (two CTAs
-                                 per SM) or 0 (default): 2 for tangent-form rotations
-                                 (gauge-Higgs), 3 for Walsh-Hadamard passes (unitary
-                                 gauge), the faster of the two for each as measured */
+                                 per SM) or 0 (default).  CTA-staged kernel: 0 is 2
+                                 for tangent-form rotations (gauge-Higgs), 3 for
+                                 Walsh-Hadamard passes (unitary gauge), the faster of
+                                 the two for each as measured.  Warp-local kernel
+                                 (QS_OPT_SHARED_KERNEL): 0 is one CTA of 24 warps per
+                                 SM with six buffers; 2 and 3 use CTAs of 8 warps */
     QS_OPT_PLAN = 11,         /* pass plan of the tiled X layer: how many new qubits
                                  each pass after the first fuses (the first pass always
                                  takes qubits 0..11).  Value: one 4-bit field per pass,
@@ -127,11 +130,18 @@ typedef enum {
                                  low qubits, 2^(12-k) amplitudes per row); 0 (default):
                                  8 per pass, the remainder last.  Rejected (QS_ERR_ARG)
                                  for states of fewer than 13 qubits.                  */
-    QS_OPT_SCAN_BUFFERS = 12  /* qs_scan_mixed: 32 KB tile buffers per CTA of the
+    QS_OPT_SCAN_BUFFERS = 12, /* qs_scan_mixed: 32 KB tile buffers per CTA of the
                                  larger lattice's passes, 2 or 3 (two CTAs per SM) or 4
                                  or 6 (one CTA per SM; a pass keeps buffers - 1 loads in
                                  flight); 0: the default, 3 (with one scratch slot
                                  per CTA, 2 x SMs slots, measured fastest)            */
+    QS_OPT_SHARED_KERNEL = 13 /* shared rotation passes (gauge-Higgs, QS_OPT_XMERGE):
+                                 1 (default): warp-local slices where the pass allows
+                                 them (its rotated qubits on tile bits 4..11, one
+                                 state, bulk stores): seven warps each take a 512-
+                                 amplitude slice of a tile through both rounds with
+                                 warp-level synchronisation only, an eighth issues
+                                 the TMA copies; 0: the CTA-staged kernel            */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open
@@ -243,12 +253,13 @@ qs_status qs_dos(qs_sim *sim, double *out);
 
 /* Autotuner: times n_steps second-order steps of every X-pass configuration that
  * applies (complex64: the persistent TMA kernel with 2 or 3 tile buffers for plain and
- * for shared passes and either store mode, and the register-staged kernel; complex128:
- * the register-staged kernel) on the bound state, which is overwritten, and keeps the
- * fastest (QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_TMA_STORE, QS_OPT_SHARED_BUFFERS).
+ * for shared passes and either store mode, the warp-local shared passes with 2 or 3
+ * buffers, and the register-staged kernel; complex128: the register-staged kernel) on
+ * the bound state, which is overwritten, and keeps the fastest (QS_OPT_XPASS,
+ * QS_OPT_TMA_BUFFERS, QS_OPT_TMA_STORE, QS_OPT_SHARED_BUFFERS, QS_OPT_SHARED_KERNEL).
  * Outputs the choice and its ms per step (host). */
 qs_status qs_autotune(qs_sim *sim, int n_steps, int *best_xpass, int *best_buffers, int *best_store,
-                      int *best_shared_buffers, double *best_ms_per_step);
+                      int *best_shared_buffers, int *best_shared_kernel, double *best_ms_per_step);
 
 /* Phase-diagram scan of two lattices in one persistent launch (Sec. V: the phase diagram
  * is mapped by independent adiabatic runs, Sec. III, at many coupling points).  sim12: a

@@ -19,6 +19,7 @@
 #include "lattice.h"
 #include "kernels.cuh"
 #include "xpass_tma.cuh"
+#include "xpass_wl.cuh"
 #include "adjoint.cuh"
 #include "adjoint_tma.cuh"
 #include "scan.cuh"
@@ -95,6 +96,8 @@ struct qs_sim {
     int xmerge = 1;                        // share the pass of one qubit group between factor groups
     int pdl = 1;                           // X passes launched with programmatic stream serialisation
     int nbuf_shared = 0;                   // TMA tile buffers of the shared passes (0 auto, 2 or 3)
+    int shared_kernel = 1;                 // shared rotation passes: 1 warp-local slices where they
+                                           // apply (k_xpass_wl), 0 the CTA-staged kernel
     int tan_off = 0;                       // tangent triple in the operator record
     int nX0 = 0, nX1 = 0;                  // X qubits per class
     bool tan_active = false;               // this call's X passes use the tangent form
@@ -522,15 +525,27 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
         const int nb = rec2 ? (s->nbuf_shared ? s->nbuf_shared : (tan ? 2 : 3)) : s->nbuf;
         size_t sm = tma_smem_bytes(s, nb, apply_z);
         XpassTmaKernel kern = xpass_tma_kernel(nb, s->tma_store != 0, rec2 != nullptr, tan);
+        // warp-local slices: a shared rotation pass with its Z layer whose rotated qubits
+        // all sit on local bits 4..11 (no stage-B rotation), one state, bulk stores
+        int nthreads = NT;
+        if (rec2 && tan && s->shared_kernel == 1 && apply_z && !P.hadamard && P.rot[1] == 0 &&
+            !P.stage_b && s->batch == 1 && s->tma_store && P.total_tiles < (1ll << 30)) {
+            // geometry by QS_OPT_SHARED_BUFFERS: 0 one CTA of 24 warps per SM with six
+            // buffers, 2 three CTAs of 8 warps with two, 3 two CTAs of 8 warps with three
+            const int g = s->nbuf_shared;
+            kern = g == 2 ? k_xpass_wl<2, 8, 3> : g == 3 ? k_xpass_wl<3, 8, 2> : k_xpass_wl<6, 24, 1>;
+            nthreads = g == 2 || g == 3 ? 256 : 768;
+            sm = tma_smem_bytes(s, g == 2 || g == 3 ? g : 6, true);
+        }
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nthreads, sm);
         if (per_sm < 1) per_sm = 1;
         long long g = std::min<long long>(P.total_tiles, (long long)per_sm * s->sm_count);
         // programmatic dependent launch: the pass may be scheduled while the previous
         // kernel drains; it waits (griddepcontrol.wait) before reading global memory
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)g);
-        cfg.blockDim = dim3(NT);
+        cfg.blockDim = dim3(nthreads);
         cfg.dynamicSmemBytes = sm;
         cfg.stream = s->stream;
         cudaLaunchAttribute attr[1];
@@ -972,7 +987,8 @@ qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_un
     const long long key[10] = {(long long)nops, order, n_steps, B, (long long)(uintptr_t)s->state[0],
                                (long long)(uintptr_t)s->d_rec, s->renorm_every,
                                s->xpass_impl * 16 + s->nbuf + 256 * s->tma_store + 1024 * s->xmerge +
-                                   4096 * (int)s->tan_active + 8192 * s->pdl + 16384 * s->nbuf_shared,
+                                   4096 * (int)s->tan_active + 8192 * s->pdl + 16384 * s->nbuf_shared +
+                                   65536 * s->shared_kernel,
                                s->method, (long long)s->dtype};
     if (!s->graph_exec || memcmp(key, s->graph_key, sizeof(key)) != 0) {
         if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
@@ -1306,6 +1322,12 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
             for (int v = 0; v < 8; ++v)
                 cudaFuncSetAttribute(xpass_tma_kernel(nb, v & 1, (v >> 1) & 1, (v >> 2) & 1),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(s, nb, true));
+        cudaFuncSetAttribute(k_xpass_wl<2, 8, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(s, 2, true));
+        cudaFuncSetAttribute(k_xpass_wl<3, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(s, 3, true));
+        cudaFuncSetAttribute(k_xpass_wl<6, 24, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tma_smem_bytes(s, 6, true));
         int adj64 = (int)(2 * (1 << LT) * 16 + (size_t)(s->nA + 1) * (s->nB + 1) * 16);
         cudaFuncSetAttribute(k_adj_xpass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_adj_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
@@ -1409,6 +1431,9 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
             if (value != 0 && value != 2 && value != 3)
                 FAIL(s, QS_ERR_ARG, "shared-pass TMA buffers must be 0 (by form), 2 or 3");
             s->nbuf_shared = (int)value; return QS_OK;
+        case QS_OPT_SHARED_KERNEL:
+            if (value != 0 && value != 1) FAIL(s, QS_ERR_ARG, "shared-pass kernel must be 0 or 1");
+            s->shared_kernel = (int)value; return QS_OK;
         case QS_OPT_ADJOINT:
             if (value < 0 || value > 7) FAIL(s, QS_ERR_ARG, "adjoint option must be 0..7");
             s->adj_impl = (value & 1) ? 1 : 0;
@@ -1939,19 +1964,24 @@ qs_status qs_scan_mixed(qs_sim *s12, const qs_couplings *p12, int n12, qs_sim *s
 }
 
 qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers, int *best_store,
-                      int *best_shared_buffers, double *best_ms_per_step) {
+                      int *best_shared_buffers, int *best_shared_kernel, double *best_ms_per_step) {
     qs_status st;
     if ((st = check_ready(s)) != QS_OK) return st;
     if (n_steps < 1 || n_steps > 1000) FAIL(s, QS_ERR_ARG, "n_steps must be in [1, 1000]");
-    if (!best_xpass || !best_buffers || !best_store || !best_shared_buffers || !best_ms_per_step)
+    if (!best_xpass || !best_buffers || !best_store || !best_shared_buffers || !best_shared_kernel ||
+        !best_ms_per_step)
         FAIL(s, QS_ERR_ARG, "null output");
-    struct Cand { int xpass, nbuf, store, nsh; };
+    struct Cand { int xpass, nbuf, store, nsh, skern; };
     std::vector<Cand> cands;
-    if (s->dtype == QS_C64 && s->tmaps_ok)
+    if (s->dtype == QS_C64 && s->tmaps_ok) {
         for (int nb = 2; nb <= 3; ++nb)
             for (int so = 0; so <= 1; ++so)
-                for (int ns = 2; ns <= 3; ++ns) cands.push_back({2, nb, so, ns});
-    cands.push_back({1, 2, 0, 0});
+                for (int ns = 2; ns <= 3; ++ns) cands.push_back({2, nb, so, ns, 0});
+        // warp-local shared passes (bulk stores only)
+        for (int nb = 2; nb <= 3; ++nb)
+            for (int ns : {0, 2, 3}) cands.push_back({2, nb, 1, ns, 1});
+    }
+    cands.push_back({1, 2, 0, 0, 0});
     const int saved_method = s->method, saved_profile = s->profile, saved_graph = s->use_graph;
     s->method = 0; s->profile = 0; s->use_graph = 0;
     std::vector<qs_couplings> c(s->batch, qs_couplings{1.0, 1.0, 0.6, 0.6});
@@ -1964,6 +1994,7 @@ qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers
     Cand pick = cands.back();
     for (const Cand &cd : cands) {
         s->xpass_impl = cd.xpass; s->nbuf = cd.nbuf; s->tma_store = cd.store; s->nbuf_shared = cd.nsh;
+        s->shared_kernel = cd.skern;
         if ((st = qs_init_plus(s)) != QS_OK) break;
         if ((st = qs_evolve(s, c.data(), sv.data(), 0.02, 2, 2)) != QS_OK) break;   // warm-up
         CK(s, cudaEventRecord(e0, s->stream));
@@ -1979,8 +2010,10 @@ qs_status qs_autotune(qs_sim *s, int n_steps, int *best_xpass, int *best_buffers
     s->method = saved_method; s->profile = saved_profile; s->use_graph = saved_graph;
     if (st != QS_OK) return st;
     s->xpass_impl = pick.xpass; s->nbuf = pick.nbuf; s->tma_store = pick.store; s->nbuf_shared = pick.nsh;
+    s->shared_kernel = pick.skern;
     *best_xpass = pick.xpass; *best_buffers = pick.nbuf; *best_store = pick.store;
     *best_shared_buffers = pick.nsh;
+    *best_shared_kernel = pick.skern;
     *best_ms_per_step = best / n_steps;
     return QS_OK;
 }

@@ -24,7 +24,8 @@ QS_C64, QS_C128 = 0, 1
 QS_NOALLOC_MAX_BATCH = 16     # include/qsim.h
 QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
 QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_ADJOINT, \
-    QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL, QS_OPT_SHARED_BUFFERS, QS_OPT_PLAN, QS_OPT_SCAN_BUFFERS = range(13)
+    QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL, QS_OPT_SHARED_BUFFERS, QS_OPT_PLAN, QS_OPT_SCAN_BUFFERS, \
+    QS_OPT_SHARED_KERNEL = range(14)
 
 
 class QsError(RuntimeError):
@@ -71,7 +72,8 @@ _SIGS = {
     "qs_selftest_wait": ([_P, _D], _I),
     "qs_num_links": ([_P], _I),
     "qs_dos": ([_P, _DP], _I),
-    "qs_autotune": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), _DP], _I),
+    "qs_autotune": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                     ctypes.POINTER(_I), _DP], _I),
     "qs_save": ([_P, ctypes.c_char_p], _I),
     "qs_load": ([_P, ctypes.c_char_p], _I),
     "qs_scan": ([_P, _CP, _I, _DP, _D, _I, _I, _DP], _I),
@@ -294,12 +296,12 @@ def qs_dos(sim, batch: int = 1):
 
 
 def qs_autotune(sim, n_steps: int = 20):
-    """Returns (xpass kernel, tile buffers, store mode, shared-pass tile buffers, ms per
-    step) of the fastest configuration."""
-    xp, nb, so, ns, ms = _I(), _I(), _I(), _I(), ctypes.c_double()
+    """Returns (xpass kernel, tile buffers, store mode, shared-pass tile buffers,
+    shared-pass kernel, ms per step) of the fastest configuration."""
+    xp, nb, so, ns, sk, ms = _I(), _I(), _I(), _I(), _I(), ctypes.c_double()
     _check(sim, library().qs_autotune(sim, n_steps, ctypes.byref(xp), ctypes.byref(nb), ctypes.byref(so),
-                                      ctypes.byref(ns), ctypes.byref(ms)))
-    return xp.value, nb.value, so.value, ns.value, ms.value
+                                      ctypes.byref(ns), ctypes.byref(sk), ctypes.byref(ms)))
+    return xp.value, nb.value, so.value, ns.value, sk.value, ms.value
 
 
 def qs_autotune_plan(sim, n_steps: int = 20):
@@ -486,7 +488,7 @@ class Simulator:
                 table = json.load(open(path))
             except (OSError, ValueError):
                 table = {}
-        if cache and key in table and "shared_buffers" in table[key] and "plan" in table[key]:
+        if cache and key in table and "shared_kernel" in table[key] and "plan" in table[key]:
             e = table[key]
             if self.n > 12:
                 self.set_option(QS_OPT_PLAN, plan_code(e["plan"]))
@@ -494,11 +496,12 @@ class Simulator:
             self.set_option(QS_OPT_TMA_BUFFERS, e["buffers"])
             self.set_option(QS_OPT_TMA_STORE, e["store"])
             self.set_option(QS_OPT_SHARED_BUFFERS, e["shared_buffers"])
+            self.set_option(QS_OPT_SHARED_KERNEL, e["shared_kernel"])
             return e
         plan, plan_ms = (qs_autotune_plan(self.h, n_steps) if self.n > 12 else (qs_plan(self.h), None))
-        xp, nb, so, ns, ms = qs_autotune(self.h, n_steps)
+        xp, nb, so, ns, sk, ms = qs_autotune(self.h, n_steps)
         entry = {"plan": plan, "plan_ms_per_step": plan_ms, "xpass": xp, "buffers": nb, "store": so,
-                 "shared_buffers": ns, "ms_per_step": ms}
+                 "shared_buffers": ns, "shared_kernel": sk, "ms_per_step": ms}
         if cache:
             table[key] = entry
             try:

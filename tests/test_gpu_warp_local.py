@@ -1,0 +1,125 @@
+"""Warp-local shared passes (QS_OPT_SHARED_KERNEL = 1, k_xpass_wl).
+
+A shared gauge-Higgs pass applies X of one factor group on the pass's new qubits, the
+Z layer, and X of the next factor group on the same qubits (Eq. (8): the X-type
+factors commute).  When every rotated qubit sits on tile bits 4..11 (a pass fusing at
+most 8 new qubits), the tile splits into eight 512-amplitude slices that never
+exchange data, and one warp takes a slice through both rounds.  Each amplitude
+sees the same floating-point operations in the same order as in the CTA-staged
+kernel, so the two agree bit for bit; both match the oracle within the complex64
+tolerance.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import OracleLattice, Couplings
+from oracle import core as O
+
+gpu = pytest.mark.gpu
+
+
+def _rel(got, ref):
+    got = np.asarray(got, dtype=np.complex128)
+    return (np.linalg.norm(got - ref) / np.linalg.norm(ref),
+            np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+
+def _run(Lx, Ly, plan, kern, nsh, cpl, s, dt, order, psi0=None, renorm=0):
+    import torch
+    from paper_2108_13410_gb300 import Simulator, QS_OPT_RENORM_EVERY
+    from paper_2108_13410_gb300.qsim import (QS_OPT_PLAN, QS_OPT_SHARED_BUFFERS, QS_OPT_SHARED_KERNEL,
+                                             plan_code)
+    sim = Simulator(Lx, Ly, form="gh", dtype="c64")
+    if plan is not None:
+        sim.set_option(QS_OPT_PLAN, plan_code(plan))
+    sim.set_option(QS_OPT_SHARED_KERNEL, kern)
+    sim.set_option(QS_OPT_SHARED_BUFFERS, nsh)
+    if renorm:
+        sim.set_option(QS_OPT_RENORM_EVERY, renorm)
+    if psi0 is None:
+        sim.init_plus()
+    else:
+        sim.upload(torch.from_numpy(psi0.reshape(1, -1)).to(torch.complex64))
+    sim.evolve([cpl], s, dt, order)
+    return sim.download()[0].numpy()
+
+
+@gpu
+@pytest.mark.parametrize("plan", [[12, 8, 4], [12, 4, 8], [12, 6, 6], [12, 7, 5], [12, 5, 7]])
+@pytest.mark.parametrize("order,n_steps", [(2, 3), (1, 2)])
+def test_plans_match_the_oracle_and_the_cta_staged_kernel(plan, order, n_steps):
+    """2x4 torus, 24 qubits, every pass fusing 4 to 8 new qubits (pass rotations on
+    one register layout only, k = 4, or on both): the warp-local shared passes give the
+    oracle's amplitudes and the CTA-staged kernel's bits."""
+    lat = OracleLattice(2, 4, True, "gh")
+    T = 0.2 * n_steps
+    s = O.schedule_linear(T, n_steps)
+    ref = O.evolve(lat, Couplings(0.7, 0.4), s, T / n_steps, order)
+    cta = _run(2, 4, plan, 0, 2, (0.7, 0.4), s, T / n_steps, order)
+    for geometry in (0, 2):
+        wl = _run(2, 4, plan, 1, geometry, (0.7, 0.4), s, T / n_steps, order)
+        rel, mx = _rel(wl, ref)
+        assert rel <= 1e-5 and mx <= 1e-5, (geometry, rel, mx)
+        assert np.array_equal(wl.view(np.uint32), cta.view(np.uint32)), geometry
+
+
+@gpu
+@pytest.mark.parametrize("nsh", [0, 2, 3])
+def test_random_state_fourier_schedule_renormalisation(nsh):
+    """3x2 torus (18 qubits: a plain pass and a shared pass fusing 6 new qubits), a
+    random complex64 start, a Fourier schedule and renormalisation every 2 steps, in
+    the three geometries (one CTA of 24 warps per SM with six tile buffers; three or
+    two CTAs of 8 warps with two or three buffers)."""
+    lat = OracleLattice(3, 2, True, "gh")
+    T, n = 1.0, 7
+    s = O.schedule_fourier(T, n, synth.fourier_coeffs(4, seed=11, std=0.05))
+    psi0 = synth.random_state(lat.n_qubits, seed=5)
+    got = _run(3, 2, None, 1, nsh, (0.9, 0.5), s, T / n, 2, psi0=psi0, renorm=2)
+    ref = O.evolve(lat, Couplings(0.9, 0.5), s, T / n, 2, psi0=psi0)
+    rel, mx = _rel(got, ref / np.linalg.norm(ref))
+    assert rel <= 1e-5 and mx <= 1e-5, (rel, mx)
+    cta = _run(3, 2, None, 0, nsh or 2, (0.9, 0.5), s, T / n, 2, psi0=psi0, renorm=2)
+    assert np.array_equal(got.view(np.uint32), cta.view(np.uint32))
+
+
+@gpu
+def test_27_qubit_kernels_agree_bit_for_bit_and_match_the_oracle_slice():
+    """3x3 torus, 27 qubits (plan 12 + 8 + 7): 12 second-order steps with each shared
+    kernel.  The tau = 0 slice equals the 18-qubit unitary-gauge oracle run
+    (psi_UG = 2^{9/2} psi_GH(sigma, tau = 0)), and the two kernels agree bit for bit on
+    the whole state."""
+    import torch
+    from paper_2108_13410_gb300 import Simulator
+    from paper_2108_13410_gb300.qsim import QS_OPT_SHARED_KERNEL
+    ug = OracleLattice(3, 3, True, "ug")
+    s = O.schedule_linear(20.0, 1000)[:12]
+    ref = O.evolve(ug, Couplings(0.6, 0.6), s, 0.02, 2)
+    digests = []
+    for kern in (1, 0):
+        sim = Simulator(3, 3, form="gh", dtype="c64")
+        sim.set_option(QS_OPT_SHARED_KERNEL, kern)
+        sim.init_plus()
+        sim.evolve([(0.6, 0.6)], s, 0.02, 2)
+        st = sim.state[0]
+        if kern == 1:
+            sl = st[: 1 << 18].cpu().numpy().astype(np.complex128) * 2 ** 4.5
+            rel, mx = _rel(sl, ref)
+            assert rel <= 1e-5 and mx <= 1e-5, (rel, mx)
+        v = torch.view_as_real(st).view(torch.int32).to(torch.int64)
+        w = torch.arange(v.numel(), device=v.device, dtype=torch.int64).view(v.shape) % 65521 + 1
+        digests.append(int((v * w).sum().item()))
+        del sim, st, v, w
+        torch.cuda.empty_cache()
+    assert digests[0] == digests[1]
+
+
+@gpu
+def test_option_is_validated():
+    from paper_2108_13410_gb300 import Simulator
+    from paper_2108_13410_gb300 import qsim as Q
+    sim = Simulator(2, 4, form="gh", dtype="c64")
+    for bad in (-1, 2):
+        with pytest.raises(Q.QsError) as e:
+            sim.set_option(Q.QS_OPT_SHARED_KERNEL, bad)
+        assert e.value.status == 1
