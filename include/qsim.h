@@ -135,13 +135,15 @@ typedef enum {
                                  or 6 (one CTA per SM; a pass keeps buffers - 1 loads in
                                  flight); 0: the default, 3 (with one scratch slot
                                  per CTA, 2 x SMs slots, measured fastest)            */
-    QS_OPT_SHARED_KERNEL = 13 /* shared rotation passes (gauge-Higgs, QS_OPT_XMERGE):
-                                 1 (default): warp-local slices where the pass allows
-                                 them (its rotated qubits on tile bits 4..11, one
-                                 state, bulk stores): seven warps each take a 512-
-                                 amplitude slice of a tile through both rounds with
-                                 warp-level synchronisation only, an eighth issues
-                                 the TMA copies; 0: the CTA-staged kernel            */
+    QS_OPT_SHARED_KERNEL = 13 /* shared X passes (QS_OPT_XMERGE; both forms) and shared
+                                 reverse passes of the complex64 adjoint: 1 (default):
+                                 warp-local slices where the pass allows them (its
+                                 rotated qubits on tile bits 4..11, one state, bulk
+                                 stores): each consumer warp takes 512-amplitude
+                                 slices of a tile through both rounds with warp-level
+                                 synchronisation only, one thread issues the TMA
+                                 copies over pooled tile buffers; 0: the CTA-staged
+                                 kernels                                              */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open

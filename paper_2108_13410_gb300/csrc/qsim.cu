@@ -22,6 +22,7 @@
 #include "xpass_wl.cuh"
 #include "adjoint.cuh"
 #include "adjoint_tma.cuh"
+#include "adjoint_wl.cuh"
 #include "scan.cuh"
 #include "scan_mixed.cuh"
 
@@ -491,6 +492,7 @@ AdjKernel adj_tma_kernel(int nbuf, bool tan, bool merged = false, bool early = f
                : k_adj_tma<2, false, false, false>;
 }
 
+
 // One X pass.  rec2 != nullptr selects the merged TMA pass: X of the pass's qubits from
 // rec, the Z layer of rec, then X of the same qubits from rec2 (the next factor group).
 template <typename R>
@@ -528,12 +530,18 @@ qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int fra
         // warp-local slices: a shared rotation pass with its Z layer whose rotated qubits
         // all sit on local bits 4..11 (no stage-B rotation), one state, bulk stores
         int nthreads = NT;
-        if (rec2 && tan && s->shared_kernel == 1 && apply_z && !P.hadamard && P.rot[1] == 0 &&
-            !P.stage_b && s->batch == 1 && s->tma_store && P.total_tiles < (1ll << 30)) {
+        const bool wl_form = (tan && !P.hadamard) || (P.hadamard && !(frame & 1));
+        if (rec2 && wl_form && s->shared_kernel == 1 && apply_z && P.rot[1] == 0 && !P.stage_b &&
+            s->batch == 1 && s->tma_store && P.total_tiles < (1ll << 30)) {
             // geometry by QS_OPT_SHARED_BUFFERS: 0 one CTA of 24 warps per SM with six
             // buffers, 2 three CTAs of 8 warps with two, 3 two CTAs of 8 warps with three
             const int g = s->nbuf_shared;
-            kern = g == 2 ? k_xpass_wl<2, 8, 3> : g == 3 ? k_xpass_wl<3, 8, 2> : k_xpass_wl<6, 24, 1>;
+            if (P.hadamard)
+                kern = g == 2 ? k_xpass_wl<2, 8, 3, true> : g == 3 ? k_xpass_wl<3, 8, 2, true>
+                                                                 : k_xpass_wl<6, 24, 1, true>;
+            else
+                kern = g == 2 ? k_xpass_wl<2, 8, 3, false> : g == 3 ? k_xpass_wl<3, 8, 2, false>
+                                                                  : k_xpass_wl<6, 24, 1, false>;
             nthreads = g == 2 || g == 3 ? 256 : 768;
             sm = tma_smem_bytes(s, g == 2 || g == 3 ? g : 6, true);
         }
@@ -1148,9 +1156,23 @@ qs_status adjoint_impl(qs_sim *s, const qs_couplings *c, const double *sv, doubl
                     }
                     carry_done[0] = d2[0];
                     carry_done[1] = d2[1];
-                    adj_kern_m<<<Gt, adj_threads, adj_smem, s->stream>>>(
-                        (float2 *)s->state[0], (float2 *)s->state[1], rec, s->rec_stride, s->n - LT, s->d_err, part_j,
-                        (int)nblk_t, i * (int)Gt, 0, rec_prev, part_prev, 0, s->tmaps[p], s->tmaps_aux[p], P);
+                    if (s->shared_kernel == 1 && B == 1 && P.rot[1] == 0 && !P.stage_b && P.frame == 1 &&
+                        P.total_tiles < (1ll << 30)) {
+                        // warp-local slices: one CTA of 12 warps per SM (11 consumers, 155
+                        // registers), three pair buffers, each reloaded once its store has read
+                        // it (measured against 10, 11, 14 and 16 warps and the later reload)
+                        const size_t wsm = 2 * (size_t)TMA_TILE_BYTES * 3 + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8;
+                        const unsigned gw = (unsigned)std::min<long long>(P.total_tiles, (long long)s->sm_count);
+                        k_adj_wl<3, 12, 1, 0><<<gw, 384, wsm, s->stream>>>(
+                            (float2 *)s->state[0], (float2 *)s->state[1], rec, s->rec_stride, s->n - LT, s->d_err,
+                            part_j, (int)nblk_t, i * (int)Gt, 0, rec_prev, part_prev, 0, s->tmaps[p], s->tmaps_aux[p],
+                            P);
+                    } else {
+                        adj_kern_m<<<Gt, adj_threads, adj_smem, s->stream>>>(
+                            (float2 *)s->state[0], (float2 *)s->state[1], rec, s->rec_stride, s->n - LT, s->d_err,
+                            part_j, (int)nblk_t, i * (int)Gt, 0, rec_prev, part_prev, 0, s->tmaps[p], s->tmaps_aux[p],
+                            P);
+                    }
                     next_carried = true;
                     dir ^= 1;
                 } else {
@@ -1322,12 +1344,16 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
             for (int v = 0; v < 8; ++v)
                 cudaFuncSetAttribute(xpass_tma_kernel(nb, v & 1, (v >> 1) & 1, (v >> 2) & 1),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(s, nb, true));
-        cudaFuncSetAttribute(k_xpass_wl<2, 8, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tma_smem_bytes(s, 2, true));
-        cudaFuncSetAttribute(k_xpass_wl<3, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tma_smem_bytes(s, 3, true));
-        cudaFuncSetAttribute(k_xpass_wl<6, 24, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)tma_smem_bytes(s, 6, true));
+        cudaFuncSetAttribute(k_adj_wl<3, 12, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * (size_t)TMA_TILE_BYTES * 3 + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
+        for (int h = 0; h < 2; ++h) {
+            cudaFuncSetAttribute(h ? k_xpass_wl<2, 8, 3, true> : k_xpass_wl<2, 8, 3, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(s, 2, true));
+            cudaFuncSetAttribute(h ? k_xpass_wl<3, 8, 2, true> : k_xpass_wl<3, 8, 2, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(s, 3, true));
+            cudaFuncSetAttribute(h ? k_xpass_wl<6, 24, 1, true> : k_xpass_wl<6, 24, 1, false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(s, 6, true));
+        }
         int adj64 = (int)(2 * (1 << LT) * 16 + (size_t)(s->nA + 1) * (s->nB + 1) * 16);
         cudaFuncSetAttribute(k_adj_xpass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);
         cudaFuncSetAttribute(k_adj_xpass<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, adj64);

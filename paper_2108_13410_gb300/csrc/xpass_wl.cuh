@@ -1,9 +1,12 @@
-// xpass_wl.cuh -- shared X pass with warp-local slices (complex64, gauge-Higgs,
-// tangent form; sm_103a).
+// xpass_wl.cuh -- shared X pass with warp-local slices (complex64; sm_103a).
 //
-// Same operator as k_xpass_tma<.., MERGED = true, TAN = true>: X of one factor group on
-// the pass's new qubits, the whole diagonal Z layer, X of the next factor group on the
-// same qubits (Eq. (8): all X-type factors commute).  It applies to passes whose
+// Same operator as k_xpass_tma<.., MERGED = true, ..>.  Gauge-Higgs (tangent-form
+// rotations): X of one factor group on the pass's new qubits, the whole diagonal Z
+// layer, X of the next factor group on the same qubits (Eq. (8): all X-type factors
+// commute).  Unitary gauge (HAD: unnormalised Walsh-Hadamard butterflies): H on the
+// pass's qubits, a diagonal table (the Hadamard-basis X layer D_X, or the Z layer), H
+// again, with the table's scale (2^-n after the two transforms of D_X).  It applies to
+// passes whose
 // rotated qubits all sit on local bits 4..11 of the 4096-amplitude tile (a pass fusing
 // k <= 8 new qubits keeps a chunk of 12 - k >= 4 unrotated low bits).  Then local bits
 // 1..3 never take part in a butterfly, and the tile splits into eight slices of 512
@@ -50,8 +53,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// NBUF tile buffers, NW warps (NW - 1 consumers), MINB resident CTAs per SM.
-template <int NBUF, int NW, int MINB>
+// NBUF tile buffers, NW warps (NW - 1 consumers), MINB resident CTAs per SM; HAD:
+// Walsh-Hadamard butterflies instead of tangent-form rotations.
+template <int NBUF, int NW, int MINB, bool HAD>
 __global__ void __launch_bounds__(32 * NW, MINB) k_xpass_wl(float2 *__restrict__ psi,
                                                                    const double *__restrict__ recs,
                                                                    const double *__restrict__ recs2,
@@ -102,8 +106,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_xpass_wl(float2 *__restrict__
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
     // operator records of the single batch element: tangent constants of both rounds,
-    // phase table scaled by the cos factors of the X layer
-    if (t < 2 * 3 * RB) {
+    // phase table scaled by the cos factors of the X layer (Walsh-Hadamard passes: the
+    // record's table as it is)
+    if (!HAD && t < 2 * 3 * RB) {
         const int round = t / (3 * RB), st = (t / RB) % 3, k = t % RB;
         const double *rr = round ? recs2 : recs;
         const float tv = (float)rr[P.tan_off + ((P.cls[st] >> k) & 1)];
@@ -112,8 +117,9 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_xpass_wl(float2 *__restrict__
     }
     const int nB1 = P.nB + 1;
     const int nlut = (P.nA + 1) * nB1;
+    const int loff = HAD ? P.lut_off : P.tan_off + 4;
     for (int i = t; i < nlut; i += NTH)
-        lut[i] = make_float2((float)recs[P.tan_off + 4 + 2 * i], (float)recs[P.tan_off + 4 + 2 * i + 1]);
+        lut[i] = make_float2((float)recs[loff + 2 * i], (float)recs[loff + 2 * i + 1]);
     __syncthreads();
 
     const int n_my = first < T ? (T - first + G - 1) / G : 0;   // tiles of this CTA
@@ -209,7 +215,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_xpass_wl(float2 *__restrict__
                     v[r] = pk(x.x, x.y);
                 }
             }
-            rotate_ts(v, P.rot[0], s_tc[0][0]);
+            if (HAD) hadamard_w(v, P.rot[0]); else rotate_ts(v, P.rot[0], s_tc[0][0]);
             __syncwarp();
 #pragma unroll
             for (int r = 0; r < NR; ++r)
@@ -218,7 +224,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_xpass_wl(float2 *__restrict__
             // ---- L2 from the exchange layout; round 1 on local 4..7, Z layer, round 2 ----
 #pragma unroll
             for (int r = 0; r < NR; ++r) v[r] = *reinterpret_cast<const u64 *>(tb + ((base_2 ^ ((r & 7) * 0x90)) + ((r >> 3) << 10)));
-            rotate_ts(v, P.rot[2], s_tc[0][2]);
+            if (HAD) hadamard_w(v, P.rot[2]); else rotate_ts(v, P.rot[2], s_tc[0][2]);
             {
                 const uint2 e0 = ptab[tile & 255], e1 = ptab[256 + ((tile >> 8) & 255)],
                             e2 = ptab[512 + ((tile >> 16) & 255)];
@@ -241,7 +247,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_xpass_wl(float2 *__restrict__
                     }
                 }
             }
-            rotate_ts(v, P.rot[2], s_tc[1][2]);
+            if (HAD) hadamard_w(v, P.rot[2]); else rotate_ts(v, P.rot[2], s_tc[1][2]);
 #pragma unroll
             for (int r = 0; r < NR; ++r)
                 *reinterpret_cast<u64 *>(tb + ((base_2 ^ ((r & 7) * 0x90)) + ((r >> 3) << 10))) = v[r];
@@ -250,7 +256,7 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_xpass_wl(float2 *__restrict__
 #pragma unroll
             for (int r = 0; r < NR; ++r)
                 v[r] = *reinterpret_cast<const u64 *>(tb + ((base_t ^ ((r & 7) * 0x90)) + ((r >> 3) << 14) + ((r & 7) << 11)));
-            rotate_ts(v, P.rot[0], s_tc[1][0]);
+            if (HAD) hadamard_w(v, P.rot[0]); else rotate_ts(v, P.rot[0], s_tc[1][0]);
             if (P.frame & 4) {
                 const int k0 = -(__popc(lane) + __popc(w) + pc_tile);
 #pragma unroll

@@ -123,3 +123,85 @@ def test_option_is_validated():
         with pytest.raises(Q.QsError) as e:
             sim.set_option(Q.QS_OPT_SHARED_KERNEL, bad)
         assert e.value.status == 1
+
+
+@gpu
+@pytest.mark.parametrize("plan", [[12, 8, 4], [12, 4, 8], [12, 6, 6]])
+@pytest.mark.parametrize("order,n_steps", [(2, 3), (1, 2)])
+def test_unitary_gauge_walsh_hadamard_passes(plan, order, n_steps):
+    """3x4 torus in unitary gauge (24 qubits): the shared passes H D_X H and H Z H'
+    (Walsh-Hadamard butterflies around the Hadamard-basis X table, with its 2^-24
+    scale, or the Z table) on the warp-local kernel give the oracle's amplitudes and the
+    CTA-staged kernel's bits."""
+    from paper_2108_13410_gb300 import Simulator
+    from paper_2108_13410_gb300.qsim import QS_OPT_PLAN, QS_OPT_SHARED_KERNEL, plan_code
+    lat = OracleLattice(3, 4, True, "ug")
+    T = 0.2 * n_steps
+    s = O.schedule_linear(T, n_steps)
+    ref = O.evolve(lat, Couplings(0.5, 0.5), s, T / n_steps, order)
+    out = []
+    for kern in (1, 0):
+        sim = Simulator(3, 4, form="ug", dtype="c64")
+        sim.set_option(QS_OPT_PLAN, plan_code(plan))
+        sim.set_option(QS_OPT_SHARED_KERNEL, kern)
+        sim.init_plus()
+        sim.evolve([(0.5, 0.5)], s, T / n_steps, order)
+        out.append(sim.download()[0].numpy())
+    rel, mx = _rel(out[0], ref)
+    assert rel <= 1e-5 and mx <= 1e-5, (rel, mx)
+    assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
+
+
+@gpu
+@pytest.mark.parametrize("T,n", [(2.0, 16), (8.0, 6)])
+def test_shared_reverse_passes_match_the_oracle_gradient(T, n):
+    """Adjoint on the 3x2 torus (18 qubits; the shared reverse pass fuses 6 qubits) with
+    the warp-local shared reverse pass: the gradient of the energy with respect to every
+    s_k within the complex64 tolerance (1e-3 of the largest oracle component), the value
+    within 1e-4 relative, psi uncomputed back to |+>; the CTA-staged reverse pass gives
+    the same value bit for bit (same forward) and the gradient up to float summation
+    order.  T = 2, 16 steps runs the tangent form (shared reverse passes); T = 8, 6 steps
+    (X angles near 1) the (u, s) rotations without shared reverse passes."""
+    from paper_2108_13410_gb300 import Simulator
+    from paper_2108_13410_gb300.qsim import QS_OPT_SHARED_KERNEL
+    lat = OracleLattice(3, 2, True, "gh")
+    s = O.schedule_fourier(T, n, synth.fourier_coeffs(4, seed=7, std=0.05))
+    e_ref, g_ref = O.energy_gradient(lat, Couplings(0.6, 0.6), s, T / n, 2, np.eye(n))
+    res = []
+    for kern in (1, 0):
+        sim = Simulator(3, 2, form="gh", dtype="c64", aux=True)
+        sim.set_option(QS_OPT_SHARED_KERNEL, kern)
+        sim.init_plus()
+        val, g = sim.adjoint_grad([(0.6, 0.6)], s, T / n, 2)
+        res.append((val[0], g[0]))
+        if kern == 1:
+            assert abs(val[0] - e_ref) <= 1e-4 * abs(e_ref)
+            scale = np.max(np.abs(g_ref))
+            assert np.max(np.abs(g[0] - g_ref)) <= 1e-3 * scale
+            psi0 = sim.download()[0].numpy().astype(np.complex128)
+            assert np.linalg.norm(psi0 - O.plus_state(lat.n_qubits)) <= 1e-4
+    assert res[0][0] == res[1][0]
+    assert np.max(np.abs(res[0][1] - res[1][1])) <= 1e-5 * np.max(np.abs(res[1][1]))
+
+
+@gpu
+def test_27_qubit_shared_reverse_passes_agree():
+    """3x3 torus, 27 qubits, 40 steps of the Fourier schedule: the warp-local and the
+    CTA-staged shared reverse passes give the same value (same forward) and gradients
+    within 1e-5 of the largest component (float summation order of the terms)."""
+    import torch
+    from paper_2108_13410_gb300 import Simulator
+    from paper_2108_13410_gb300.qsim import QS_OPT_SHARED_KERNEL
+    T, n = 1.6, 40
+    s = O.schedule_fourier(T, n, synth.fourier_coeffs(8, seed=3, std=0.02))
+    res = []
+    for kern in (1, 0):
+        sim = Simulator(3, 3, form="gh", dtype="c64", aux=True)
+        sim.set_option(QS_OPT_SHARED_KERNEL, kern)
+        sim.init_plus()
+        val, g = sim.adjoint_grad([(0.6, 0.6)], s, T / n, 2)
+        res.append((val[0], g[0]))
+        del sim
+        torch.cuda.empty_cache()
+    assert res[0][0] == res[1][0]
+    assert np.max(np.abs(res[0][1] - res[1][1])) <= 1e-5 * np.max(np.abs(res[1][1]))
