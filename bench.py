@@ -309,7 +309,7 @@ def run_ours(args):
              "k_xpass_tma<%d, %s, true, true>" % (tune["shared_buffers"] or 2, tb(tune["store"])))
     tags = ("k_xpass_tma_c64_27q", "k_xpass_tma_shared_c64_27q")
     if tune["shared_kernel"] == 1 and tune["store"]:  # warp-local shared passes
-        geom = {0: "6, 24, 1", 2: "2, 8, 3", 3: "3, 8, 2"}[tune["shared_buffers"]]
+        geom = {0: "6, 24, 1, false", 2: "2, 8, 3, false", 3: "3, 8, 2, false"}[tune["shared_buffers"]]
         names = (names[0], "k_xpass_wl<%s>" % geom)
         tags = (tags[0], "k_xpass_wl_c64_27q")
     if tune["xpass"] == 1:                            # the register-staged kernel (no shared passes)
@@ -522,8 +522,12 @@ def ug32_leg(local, dev, stream):
     peak, _ = peaks()
     out = {"lattice": "4x4 periodic", "form": "unitary gauge", "qubits": 32, "g": 0.5, "lambda": 0.5,
            "dt": 0.02, "order": 2}
-    for dtype, n in (("c64", 10), ("c128", 2)):
+    from paper_2108_13410_gb300.qsim import QS_OPT_C128_DF
+    # complex128: the double-float passes (default) and the FP64 register kernel
+    for key, dtype, n, df in (("c64", "c64", 10, 1), ("c128", "c128", 10, 1), ("c128_fp64", "c128", 2, 0)):
         sim = Simulator(4, 4, form="ug", dtype=dtype, device=f"cuda:{local}")
+        if dtype == "c128":
+            sim.set_option(QS_OPT_C128_DF, df)
         sim.init_plus()
         sim.evolve(cpl, s[:2], 0.02, 2)
         torch.cuda.synchronize(dev)
@@ -547,10 +551,25 @@ def ug32_leg(local, dev, stream):
                 gbs = alg / (kms / kn / 1000.0) / 1e9
                 kern[name] = {"launches": kn, "avg_launch_ms": kms / kn, "achieved_gbs": gbs, "frac": gbs / peak}
         npass = kinds[0][1] + kinds[1][1]
-        out[dtype] = {"steps": n, "steps_per_s": n / (ms / 1000.0), "ms_per_step": ms / n,
-                      "state_bytes": sim.state_bytes, "passes_per_step": npass / n, "launches": launches,
-                      "xpass": kern, "step_hbm_gbs": npass * alg / (ms / 1000.0) / 1e9,
-                      "norm_minus_1": float(sim.expect(QS_NORM)[0] - 1.0)}
+        out[key] = {"steps": n, "steps_per_s": n / (ms / 1000.0), "ms_per_step": ms / n,
+                    "state_bytes": sim.state_bytes, "passes_per_step": npass / n, "launches": launches,
+                    "xpass": kern, "step_hbm_gbs": npass * alg / (ms / 1000.0) / 1e9,
+                    "norm_minus_1": float(sim.expect(QS_NORM)[0] - 1.0)}
+        if key == "c128":
+            # the in-place split into the blocked double-float layout and the join back run
+            # once per call, inside the time above; a one-step call separates them:
+            # t(n) = n step + c, t(1) = step + c
+            e0.record(stream)
+            sim.evolve(cpl, s[2 + n:3 + n], 0.02, 2)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            t1 = e0.elapsed_time(e1)
+            step = (ms - t1) / (n - 1)
+            out[key]["arithmetic"] = "double-float (two floats per real number, FP32 pipes)"
+            out[key]["split_join_ms_per_call"] = t1 - step
+            out[key]["ms_per_step_without_split_join"] = step
+        elif key == "c128_fp64":
+            out[key]["arithmetic"] = "FP64"
         del sim
         torch.cuda.empty_cache()
     return out

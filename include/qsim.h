@@ -135,7 +135,7 @@ typedef enum {
                                  or 6 (one CTA per SM; a pass keeps buffers - 1 loads in
                                  flight); 0: the default, 3 (with one scratch slot
                                  per CTA, 2 x SMs slots, measured fastest)            */
-    QS_OPT_SHARED_KERNEL = 13 /* shared X passes (QS_OPT_XMERGE; both forms) and shared
+    QS_OPT_SHARED_KERNEL = 13,/* shared X passes (QS_OPT_XMERGE; both forms) and shared
                                  reverse passes of the complex64 adjoint: 1 (default):
                                  warp-local slices where the pass allows them (its
                                  rotated qubits on tile bits 4..11, one state, bulk
@@ -144,6 +144,13 @@ typedef enum {
                                  synchronisation only, one thread issues the TMA
                                  copies over pooled tile buffers; 0: the CTA-staged
                                  kernels                                              */
+    QS_OPT_C128_DF = 14       /* complex128, unitary gauge, fused kernels: 1 (default):
+                                 the Walsh-Hadamard passes run in double-float
+                                 arithmetic (each real number an unevaluated sum of two
+                                 floats, 48 significand bits, on the FP32 pipes; the
+                                 state is converted in place to a blocked layout at the
+                                 start of a call and back at its end); 0: FP64
+                                 register-staged passes                               */
 } qs_option;
 
 /* Create a simulator for an Lx x Ly lattice.  Periodic needs Lx, Ly >= 2; open

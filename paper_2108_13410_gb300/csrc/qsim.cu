@@ -20,6 +20,7 @@
 #include "kernels.cuh"
 #include "xpass_tma.cuh"
 #include "xpass_wl.cuh"
+#include "xpass_df.cuh"
 #include "adjoint.cuh"
 #include "adjoint_tma.cuh"
 #include "adjoint_wl.cuh"
@@ -109,6 +110,12 @@ struct qs_sim {
     std::vector<CUtensorMap> tmaps;        // one per pass, encoded for the bound state
     bool tmaps_ok = false;
     std::vector<CUtensorMap> tmaps_aux;    // the same over the adjoint work state (slot 1)
+    // complex128 unitary-gauge passes in double-float arithmetic (xpass_df.cuh): tensor
+    // maps of the high and low halves of the blocked layout, one pair per pass
+    std::vector<CUtensorMap> tmaps_dfh, tmaps_dfl;
+    bool tmaps_df_ok = false;
+    int c128_df = 1;                       // QS_OPT_C128_DF
+    bool df_active = false;                // the state is in the blocked layout (inside a call)
     bool tmaps_aux_ok = false;
     int *d_err = nullptr;                  // device flag: bounded wait gave up
     // adjoint workspaces
@@ -322,7 +329,9 @@ qs_status encode_tmaps(qs_sim *s, int slot = 0) {
     bool &ok = slot == 0 ? s->tmaps_ok : s->tmaps_aux_ok;
     ok = false;
     maps.clear();
-    if (s->dtype != QS_C64 || s->passes.empty() || !s->state[slot]) return QS_OK;
+    if (slot == 0) { s->tmaps_df_ok = false; s->tmaps_dfh.clear(); s->tmaps_dfl.clear(); }
+    if (s->passes.empty() || !s->state[slot]) return QS_OK;
+    if (s->dtype != QS_C64 && !(s->dtype == QS_C128 && slot == 0)) return QS_OK;
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -333,6 +342,30 @@ qs_status encode_tmaps(qs_sim *s, int slot = 0) {
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
     const int n = s->n;
+    if (s->dtype == QS_C128) {
+        // blocked double-float layout: per 16 amplitudes, 16 high (re, im) float pairs then
+        // 16 low ones; each half is a complex64-like tile with doubled strides
+        for (size_t p = 0; p < s->passes.size(); ++p) {
+            const TmaPass &P = s->tpasses[NVAR * p];
+            cuuint64_t dims[5] = {16, 1ull << (P.c - 4), 1ull << (P.next - P.c), 1ull << P.k,
+                                  (1ull << (n - P.next - P.k)) * (cuuint64_t)s->batch};
+            cuuint64_t strides[4] = {16 * 16, (1ull << P.c) * 16, (1ull << P.next) * 16, (1ull << (P.next + P.k)) * 16};
+            cuuint32_t box[5] = {16, (cuuint32_t)(1u << (P.c - 4)), 1, (cuuint32_t)(1u << P.k), 1};
+            cuuint32_t es[5] = {1, 1, 1, 1, 1};
+            for (int half = 0; half < 2; ++half) {
+                CUtensorMap m;
+                CUresult r = encode(&m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5,
+                                    (char *)s->state[0] + 128 * half, dims, strides, box, es,
+                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                if (r != CUDA_SUCCESS)
+                    FAIL(s, QS_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for double-float pass %zu", (int)r, p);
+                (half ? s->tmaps_dfl : s->tmaps_dfh).push_back(m);
+            }
+        }
+        s->tmaps_df_ok = true;
+        return QS_OK;
+    }
     for (size_t p = 0; p < s->passes.size(); ++p) {
         const TmaPass &P = s->tpasses[NVAR * p];
         cuuint64_t dims[5] = {16, 1ull << (P.c - 4), 1ull << (P.next - P.c), 1ull << P.k,
@@ -493,11 +526,73 @@ AdjKernel adj_tma_kernel(int nbuf, bool tan, bool merged = false, bool early = f
 }
 
 
+// One complex128 Walsh-Hadamard pass in double-float arithmetic over the blocked layout
+// (variants V_HAD, V_HAD_X, V_HAD_Z; merged: a second round of butterflies).
+size_t df_smem_bytes(const qs_sim *s) {
+    return 2 * (size_t)TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 32 + 3 * 256 * 8;
+}
+
+qs_status launch_xpass_df(qs_sim *s, int p, int variant, const double *rec, bool merged) {
+    TmaPass P = s->tpasses[NVAR * p + variant];
+    P.frame = 0;
+    if (!P.hadamard) FAIL(s, QS_ERR_STATE, "double-float passes run the Walsh-Hadamard form only");
+    const size_t sm = df_smem_bytes(s);
+    auto kern = merged ? k_xpass_df<true> : k_xpass_df<false>;
+    cudaEvent_t e1 = nullptr;
+    if (s->profile) {   // per-launch CUDA events, as for the complex64 passes
+        while (s->ev_pool.size() < s->ev_used + 2) {
+            cudaEvent_t e;
+            CK(s, cudaEventCreate(&e));
+            s->ev_pool.push_back(e);
+        }
+        cudaEvent_t e0 = s->ev_pool[s->ev_used];
+        e1 = s->ev_pool[s->ev_used + 1];
+        s->ev_used += 2;
+        s->ev_kind.resize(s->ev_used / 2);
+        s->ev_kind.back() = merged ? 1 : 0;
+        CK(s, cudaEventRecord(e0, s->stream));
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm);
+    if (per_sm < 1) per_sm = 1;
+    const long long g = std::min<long long>(P.total_tiles, (long long)per_sm * s->sm_count);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)g);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = s->pdl ? 1 : 0;
+    CK(s, cudaLaunchKernelEx(&cfg, kern, (float2 *)s->state[0], rec, s->rec_stride, s->n - LT, s->d_err,
+                             s->tmaps_dfh[p], s->tmaps_dfl[p], P));
+    CKL(s);
+    s->launches++;
+    if (s->profile) CK(s, cudaEventRecord(e1, s->stream));
+    return QS_OK;
+}
+
+// In-place conversion of the bound complex128 state to (to_df) or from the blocked
+// double-float layout.
+qs_status df_convert(qs_sim *s, bool to_df) {
+    const long long amps = (long long)s->batch << s->n;
+    const unsigned grid = (unsigned)std::min<long long>((amps / 32 + 7) / 8, (long long)s->sm_count * 16);
+    if (to_df) k_df_split<<<grid, 256, 0, s->stream>>>((double2 *)s->state[0], amps);
+    else k_df_join<<<grid, 256, 0, s->stream>>>((double2 *)s->state[0], amps);
+    CKL(s);
+    s->launches++;
+    s->df_active = to_df;
+    return QS_OK;
+}
+
 // One X pass.  rec2 != nullptr selects the merged TMA pass: X of the pass's qubits from
 // rec, the Z layer of rec, then X of the same qubits from rec2 (the next factor group).
 template <typename R>
 qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int frame = 0,
                        const double *rec2 = nullptr, int xscale = 0) {
+    if (sizeof(R) == 8 && s->df_active) return launch_xpass_df(s, p, variant, rec, rec2 != nullptr);
     const PassDesc &d = s->pvar[NVAR * p + variant];
     const bool apply_z = d.apply_z != 0;
     dim3 grid((unsigned)(1ll << d.nfixed), (unsigned)s->batch);
@@ -749,6 +844,11 @@ inline double res(const qs_sim *s, int slot, int b, int v) {
 template <typename R>
 qs_status renormalise(qs_sim *s) {
     qs_status st;
+    if (sizeof(R) == 8 && s->df_active) {   // blocked double-float layout: join, rescale, split
+        if ((st = df_convert(s, false)) != QS_OK) return st;
+        if ((st = renormalise<R>(s)) != QS_OK) return st;
+        return df_convert(s, true);
+    }
     if ((st = reduce_diag<R>(s, s->state[0], 0, 0)) != QS_OK) return st;
     dim3 grid(152 * 8, (unsigned)s->batch);
     k_scale_by_norm<R><<<grid, 256, 0, s->stream>>>((V<R> *)s->state[0], s->dim, s->d_res);
@@ -930,7 +1030,15 @@ qs_status launch_ops_merged_ug(qs_sim *s, const std::vector<Op> &ops, int steps_
 
 template <typename R>
 bool merged_schedule_ug(const qs_sim *s) {
+    if (sizeof(R) == 8) return s->df_active && s->xmerge && s->passes.size() >= 2;
     return sizeof(R) == 4 && s->method == 0 && s->xmerge && !s->lat.gauge_higgs && s->tmaps_ok &&
+           s->xpass_impl != 1 && s->passes.size() >= 2;
+}
+
+// complex128 unitary gauge, fused kernels: passes in double-float arithmetic
+template <typename R>
+bool df_schedule(const qs_sim *s) {
+    return sizeof(R) == 8 && s->method == 0 && s->c128_df && !s->lat.gauge_higgs && s->tmaps_df_ok &&
            s->xpass_impl != 1 && s->passes.size() >= 2;
 }
 
@@ -942,6 +1050,13 @@ qs_status launch_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm
     const size_t nops = ops.size() / B;
     if (j1 > nops) j1 = nops;
     if (merged_schedule<R>(s)) return launch_ops_merged<R>(s, ops, steps_per_renorm_unit, j0, j1);
+    if (df_schedule<R>(s) && !s->df_active) {
+        // split into the blocked double-float layout, run the passes, join back
+        if ((st = df_convert(s, true)) != QS_OK) return st;
+        st = launch_ops<R>(s, ops, steps_per_renorm_unit, j0, j1);
+        qs_status st2 = df_convert(s, false);
+        return st != QS_OK ? st : st2;
+    }
     if (merged_schedule_ug<R>(s)) return launch_ops_merged_ug<R>(s, ops, steps_per_renorm_unit, j0, j1);
     for (size_t k = j0; k < j1; ++k) {
         if (s->method == 0)
@@ -996,7 +1111,7 @@ qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_un
                                (long long)(uintptr_t)s->d_rec, s->renorm_every,
                                s->xpass_impl * 16 + s->nbuf + 256 * s->tma_store + 1024 * s->xmerge +
                                    4096 * (int)s->tan_active + 8192 * s->pdl + 16384 * s->nbuf_shared +
-                                   65536 * s->shared_kernel,
+                                   65536 * s->shared_kernel + 131072 * s->c128_df,
                                s->method, (long long)s->dtype};
     if (!s->graph_exec || memcmp(key, s->graph_key, sizeof(key)) != 0) {
         if (s->graph_exec) { cudaGraphExecDestroy(s->graph_exec); s->graph_exec = nullptr; }
@@ -1344,6 +1459,8 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
             for (int v = 0; v < 8; ++v)
                 cudaFuncSetAttribute(xpass_tma_kernel(nb, v & 1, (v >> 1) & 1, (v >> 2) & 1),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(s, nb, true));
+        cudaFuncSetAttribute(k_xpass_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df_smem_bytes(s));
+        cudaFuncSetAttribute(k_xpass_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df_smem_bytes(s));
         cudaFuncSetAttribute(k_adj_wl<3, 12, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(2 * (size_t)TMA_TILE_BYTES * 3 + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
         for (int h = 0; h < 2; ++h) {
@@ -1457,6 +1574,9 @@ qs_status qs_set_option(qs_sim *s, int key, long long value) {
             if (value != 0 && value != 2 && value != 3)
                 FAIL(s, QS_ERR_ARG, "shared-pass TMA buffers must be 0 (by form), 2 or 3");
             s->nbuf_shared = (int)value; return QS_OK;
+        case QS_OPT_C128_DF:
+            if (value != 0 && value != 1) FAIL(s, QS_ERR_ARG, "double-float option must be 0 or 1");
+            s->c128_df = (int)value; return QS_OK;
         case QS_OPT_SHARED_KERNEL:
             if (value != 0 && value != 1) FAIL(s, QS_ERR_ARG, "shared-pass kernel must be 0 or 1");
             s->shared_kernel = (int)value; return QS_OK;

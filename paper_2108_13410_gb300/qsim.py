@@ -25,7 +25,7 @@ QS_NOALLOC_MAX_BATCH = 16     # include/qsim.h
 QS_NORM, QS_PLAQUETTE, QS_WILSON, QS_X, QS_ENERGY, QS_ENERGY_S, QS_GAUSS, QS_THOOFT = range(8)
 QS_OPT_METHOD, QS_OPT_RENORM_EVERY, QS_OPT_PROFILE, QS_OPT_GRAPH, QS_OPT_XPASS, QS_OPT_TMA_BUFFERS, QS_OPT_ADJOINT, \
     QS_OPT_TMA_STORE, QS_OPT_XMERGE, QS_OPT_PDL, QS_OPT_SHARED_BUFFERS, QS_OPT_PLAN, QS_OPT_SCAN_BUFFERS, \
-    QS_OPT_SHARED_KERNEL = range(14)
+    QS_OPT_SHARED_KERNEL, QS_OPT_C128_DF = range(15)
 
 
 class QsError(RuntimeError):
