@@ -5,8 +5,12 @@
 // number of the state is carried as an unevaluated sum hi + lo of two floats (|lo| <=
 // ulp(hi) / 2, 48 significand bits), and the passes run on the FP32 pipes with packed
 // f32x2 instructions, (re, im) in one 64-bit register:
-//   * sum and difference: Knuth's two-sum (two-diff) of the high parts, the low parts
-//     added to the error, one fast renormalisation (11 packed operations per output);
+//   * sum and difference: Knuth's two-sum (two-diff) of the high parts (exact), the
+//     error and the low parts summed into the low part (8 packed operations per output).
+//     Within a pass the pairs are not renormalised after every butterfly (the low part
+//     grows by at most the pass's number of stages times an ulp of the high part, about
+//     2^-43 relative); one fast renormalisation runs before the table product and before
+//     the store;
 //   * product with a table entry (cos phi, sin phi) held in double-float: the rounding
 //     error of the high product recovered exactly by scalar FMA (fmaf, one rounding),
 //     the cross terms by packed FMA, renormalisation.  (A packed f32x2 FMA in that role
@@ -47,25 +51,6 @@ __device__ __forceinline__ u64 swap2(u64 a) {   // (x, y) -> (y, x)
     return d;
 }
 
-// (ah, al) + (bh, bl) and (ah, al) - (bh, bl), double-float, both lanes of each register
-__device__ __forceinline__ void df_butterfly(u64 &ah, u64 &al, u64 &bh, u64 &bl) {
-    // sum: two-sum of the high parts
-    const u64 s = add2(ah, bh);
-    const u64 sv = sub2(s, ah);
-    u64 e = add2(sub2(ah, sub2(s, sv)), sub2(bh, sv));
-    e = add2(e, add2(al, bl));
-    const u64 rh = add2(s, e);
-    const u64 rl = sub2(e, sub2(rh, s));
-    // difference: two-diff of the high parts
-    const u64 d = sub2(ah, bh);
-    const u64 dv = sub2(d, ah);
-    u64 f = sub2(sub2(ah, sub2(d, dv)), add2(bh, dv));
-    f = add2(f, sub2(al, bl));
-    const u64 qh = add2(d, f);
-    const u64 ql = sub2(f, sub2(qh, d));
-    ah = rh; al = rl; bh = qh; bl = ql;
-}
-
 // a * b - p per lane for p = RN(a * b): exact, by scalar FMA
 __device__ __forceinline__ u64 prod_err(u64 a, u64 b, u64 p) {
     const float2 x = unpk(a), y = unpk(b), q = unpk(p);
@@ -91,6 +76,29 @@ __device__ __forceinline__ void df_add(u64 ah, u64 al, u64 bh, u64 bl, u64 &rh, 
     rl = sub2(e, sub2(rh, s));
 }
 
+// sum and difference without renormalisation (see the header)
+__device__ __forceinline__ void df_butterfly_lazy(u64 &ah, u64 &al, u64 &bh, u64 &bl) {
+    const u64 s = add2(ah, bh);
+    const u64 sv = sub2(s, ah);
+    const u64 es = add2(sub2(ah, sub2(s, sv)), sub2(bh, sv));
+    const u64 d = sub2(ah, bh);
+    const u64 dv = sub2(d, ah);
+    const u64 ed = sub2(sub2(ah, sub2(d, dv)), add2(bh, dv));
+    const u64 ls = add2(es, add2(al, bl));
+    const u64 ld = add2(ed, sub2(al, bl));
+    ah = s; al = ls; bh = d; bl = ld;
+}
+
+// fast renormalisation of every pair: |l| <= ulp(h) / 2 afterwards
+__device__ __forceinline__ void df_renorm(u64 (&h)[NR], u64 (&l)[NR]) {
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const u64 nh = add2(h[r], l[r]);
+        l[r] = sub2(l[r], sub2(nh, h[r]));
+        h[r] = nh;
+    }
+}
+
 // unnormalised Walsh-Hadamard butterflies on the register bits of mask
 __device__ __forceinline__ void df_hadamard(u64 (&h)[NR], u64 (&l)[NR], unsigned mask) {
 #pragma unroll
@@ -98,7 +106,7 @@ __device__ __forceinline__ void df_hadamard(u64 (&h)[NR], u64 (&l)[NR], unsigned
         if (!((mask >> k) & 1u)) continue;
 #pragma unroll
         for (int r = 0; r < NR; ++r)
-            if (!((r >> k) & 1)) df_butterfly(h[r], l[r], h[r | (1 << k)], l[r | (1 << k)]);
+            if (!((r >> k) & 1)) df_butterfly_lazy(h[r], l[r], h[r | (1 << k)], l[r | (1 << k)]);
     }
 }
 
@@ -290,6 +298,7 @@ __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, 
         const long long up = tile >> P.mid_bits;
         const long long gbase = (mid << P.c) + (up << (P.next + P.k));
         if (P.apply_z) {
+            df_renorm(h, l);
             const long long tin = tile & tmask;
             const uint2 e0 = ptab[tin & 255], e1 = ptab[256 + ((tin >> 8) & 255)], e2 = ptab[512 + ((tin >> 16) & 255)];
             const uint32_t pa = pa_t ^ e0.x ^ e1.x ^ e2.x;
@@ -334,12 +343,14 @@ __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, 
             __syncthreads();
             if (t == 0 && it + 1 < n_my) issue(tile + G);
             df_hadamard(h, l, P.rot[0]);
+            df_renorm(h, l);
             // blocked layout: amplitude g = 16 m + j has its high pair at float2 index
             // 32 m + j and its low pair at 32 m + 16 + j
             dst = reinterpret_cast<u64 *>(state) + 2 * (gbase + toff_a) + tlo;
 #pragma unroll
             for (int r = 0; r < NR; ++r) { dst[2 * P.roff_a[r]] = h[r]; dst[2 * P.roff_a[r] + 16] = l[r]; }
         } else {
+            df_renorm(h, l);
             dst = reinterpret_cast<u64 *>(state) + 2 * (gbase + toff_c) + tlo;
 #pragma unroll
             for (int r = 0; r < NR; ++r) { dst[2 * P.roff_c[r]] = h[r]; dst[2 * P.roff_c[r] + 16] = l[r]; }
