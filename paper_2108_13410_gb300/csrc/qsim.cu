@@ -578,7 +578,7 @@ qs_status launch_xpass_df(qs_sim *s, int p, int variant, const double *rec, bool
 // double-float layout.
 qs_status df_convert(qs_sim *s, bool to_df) {
     const long long amps = (long long)s->batch << s->n;
-    const unsigned grid = (unsigned)std::min<long long>((amps / 32 + 7) / 8, (long long)s->sm_count * 16);
+    const unsigned grid = (unsigned)std::min<long long>((amps / 128 + 7) / 8, (long long)s->sm_count * 8);
     if (to_df) k_df_split<<<grid, 256, 0, s->stream>>>((double2 *)s->state[0], amps);
     else k_df_join<<<grid, 256, 0, s->stream>>>((double2 *)s->state[0], amps);
     CKL(s);

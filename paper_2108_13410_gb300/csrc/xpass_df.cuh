@@ -121,33 +121,86 @@ __device__ __forceinline__ void df_phase(u64 &vh, u64 &vl, const DfPhase &q) {
     df_add(ah, al, swap2(bh), swap2(bl), vh, vl);
 }
 
+// Split of a double into two floats with integer operations (GB300's FP64 conversions
+// run at the FP64 rate): hi = d with its binary fraction cut to 23 bits (truncation),
+// lo = the 29 dropped fraction bits as a float (rounded to 24 bits), so hi + lo keeps 48
+// significand bits.  |d| below 2^-126 (no normal float hi) maps to (0, 0): the state's
+// amplitudes are at most 1, so that drops less than 2^-126 absolute.
+__device__ __forceinline__ void split_double(double d, float &hi, float &lo) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    const unsigned int top = (unsigned int)(u >> 32), bot = (unsigned int)u;
+    const unsigned int sign = top & 0x80000000u;
+    const int e = (int)((top >> 20) & 0x7ffu);          // biased double exponent
+    const int E = e - 896;                               // biased float exponent of hi
+    if (e == 0x7ff || E >= 255) { hi = __double2float_rn(d); lo = 0.f; return; }   // keeps inf / NaN
+    if (E <= 0) { hi = 0.f; lo = 0.f; return; }
+    hi = __uint_as_float(sign | ((unsigned int)E << 23) | ((top & 0xfffffu) << 3) | (bot >> 29));
+    const unsigned int r = bot & 0x1fffffffu;            // dropped bits, units of 2^(e-1075)
+    const int El = e - 948;                              // biased float exponent of 2^(e-1075)
+    // below the normal range the power of two is applied in two factors (El + 64 > 12 here)
+    const float v = El > 0 ? __uint2float_rn(r) * __uint_as_float((unsigned int)El << 23)
+                           : __uint2float_rn(r) * __uint_as_float((unsigned int)(El + 64) << 23) * 0x1p-64f;
+    lo = __uint_as_float(__float_as_uint(v) | sign);
+}
+
+// hi + lo as a double: exact conversions of both floats by bit assembly, one FP64 add
+__device__ __forceinline__ double float_to_double_bits(float f) {
+    const unsigned int b = __float_as_uint(f);
+    const unsigned int E = (b >> 23) & 0xffu;
+    if (E == 0 || E == 255) return (double)f;            // zero, subnormal, inf, NaN
+    const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                 ((unsigned long long)(E + 896u) << 52) |
+                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+
 // In-place conversion of complex128 amplitudes to the blocked double-float layout and
-// back: a warp takes two 16-amplitude blocks (one amplitude per lane), reads them whole,
-// and writes them after __syncwarp, so no block is read after another lane wrote to it.
+// back: a warp takes four runs of two 16-amplitude blocks (one amplitude per lane and
+// run, four loads in flight), reads them whole, and writes them after __syncwarp, so no
+// block is read after another lane wrote to it.  n_amps is a multiple of 128.
+constexpr int DF_RUNS = 4;
+
 __global__ void k_df_split(double2 *__restrict__ state, long long n_amps) {
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     const int lane = threadIdx.x & 31;
-    for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 32 * w < n_amps; w += warps) {
-        const long long g = 32 * w + lane;
-        const double2 v = state[g];
-        const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
-        const float rl = __double2float_rn(v.x - (double)rh), il = __double2float_rn(v.y - (double)ih);
+    for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 32 * DF_RUNS * w < n_amps;
+         w += warps) {
+        double2 v[DF_RUNS];
+#pragma unroll
+        for (int k = 0; k < DF_RUNS; ++k) v[k] = state[32 * (DF_RUNS * w + k) + lane];
         __syncwarp();
-        float2 *blk = reinterpret_cast<float2 *>(state + (g & ~15ll));
-        blk[g & 15] = make_float2(rh, ih);
-        blk[16 + (g & 15)] = make_float2(rl, il);
+#pragma unroll
+        for (int k = 0; k < DF_RUNS; ++k) {
+            const long long g = 32 * (DF_RUNS * w + k) + lane;
+            float rh, rl, ih, il;
+            split_double(v[k].x, rh, rl);
+            split_double(v[k].y, ih, il);
+            float2 *blk = reinterpret_cast<float2 *>(state + (g & ~15ll));
+            blk[g & 15] = make_float2(rh, ih);
+            blk[16 + (g & 15)] = make_float2(rl, il);
+        }
     }
 }
 
 __global__ void k_df_join(double2 *__restrict__ state, long long n_amps) {
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     const int lane = threadIdx.x & 31;
-    for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 32 * w < n_amps; w += warps) {
-        const long long g = 32 * w + lane;
-        const float2 *blk = reinterpret_cast<const float2 *>(state + (g & ~15ll));
-        const float2 h = blk[g & 15], l = blk[16 + (g & 15)];
+    for (long long w = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 32 * DF_RUNS * w < n_amps;
+         w += warps) {
+        float2 h[DF_RUNS], l[DF_RUNS];
+#pragma unroll
+        for (int k = 0; k < DF_RUNS; ++k) {
+            const long long g = 32 * (DF_RUNS * w + k) + lane;
+            const float2 *blk = reinterpret_cast<const float2 *>(state + (g & ~15ll));
+            h[k] = blk[g & 15];
+            l[k] = blk[16 + (g & 15)];
+        }
         __syncwarp();
-        state[g] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
+#pragma unroll
+        for (int k = 0; k < DF_RUNS; ++k)
+            state[32 * (DF_RUNS * w + k) + lane] =
+                make_double2(float_to_double_bits(h[k].x) + float_to_double_bits(l[k].x),
+                             float_to_double_bits(h[k].y) + float_to_double_bits(l[k].y));
     }
 }
 
