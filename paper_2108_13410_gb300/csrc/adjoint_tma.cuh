@@ -234,6 +234,15 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
         x = warp_sum_f(x);
         if ((t & 31) == 0) red[t >> 5][v] += (double)x;
     };
+    // plain reverse passes: each lane keeps float sums of its four terms over eight tiles,
+    // then the warp sums them into its FP64 slots (one FP64 add per value per eight tiles)
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    int n_acc = 0;
+    auto flush_acc = [&]() {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) { add_tile(v, acc[v]); acc[v] = 0.f; }
+        n_acc = 0;
+    };
     // values 0..3 to partials, 4..7 (MERGED) to partials2
     auto flush = [&](long long bat) {
         __syncthreads();
@@ -278,6 +287,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
         const uint32_t parity = (uint32_t)((it / NBUF) & 1);
         const long long batch = tile >> tiles_shift;
         if (batch != cur_batch) {
+            if (!MERGED && n_acc) flush_acc();
             if (cur_batch >= 0) flush(cur_batch);   // the previous batch element's sums
             __syncthreads();
             const double *rec = recs + batch * rec_stride;
@@ -479,7 +489,8 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
 #pragma unroll
                 for (int r = 0; r < NR; ++r) { tp[c_idx(r)] = p[r]; tl[c_idx(r)] = l[r]; }
             }
-            add_tile(0, g0); add_tile(1, g1); add_tile(2, ga); add_tile(3, gb);
+            acc[0] += g0; acc[1] += g1; acc[2] += ga; acc[3] += gb;
+            if (++n_acc == 8) flush_acc();
         }
         if (EARLY) continue;
         // both tiles back to HBM by bulk tensor stores (same maps and boxes as the loads)
@@ -493,6 +504,7 @@ __global__ void __launch_bounds__(NT, NBUF == 1 ? 2 : 1) k_adj_tma(float2 *__res
             bulk_commit();
         }
     }
+    if (!MERGED && n_acc) flush_acc();
     if (cur_batch >= 0) flush(cur_batch);   // the last batch element's sums
     if (t == 0) bulk_wait_all();            // the CTA's shared memory must outlive its stores
 }
