@@ -532,12 +532,18 @@ size_t df_smem_bytes(const qs_sim *s) {
     return 2 * (size_t)TMA_TILE_BYTES + 1024 + (size_t)s->max_lut * 32 + 3 * 256 * 8;
 }
 
-qs_status launch_xpass_df(qs_sim *s, int p, int variant, const double *rec, bool merged) {
+qs_status launch_xpass_df(qs_sim *s, int p, int variant, const double *rec, const double *rec2, int frame,
+                          int xscale) {
     TmaPass P = s->tpasses[NVAR * p + variant];
-    P.frame = 0;
-    if (!P.hadamard) FAIL(s, QS_ERR_STATE, "double-float passes run the Walsh-Hadamard form only");
+    const bool merged = rec2 != nullptr;
+    const bool rot = !P.hadamard;
+    P.frame = rot ? frame : 0;
+    P.xscale = rot ? xscale : 0;
+    if (rot && !(s->tan_active && (frame & 1)))
+        FAIL(s, QS_ERR_STATE, "double-float rotation passes run the tangent form only");
     const size_t sm = df_smem_bytes(s);
-    auto kern = merged ? k_xpass_df<true> : k_xpass_df<false>;
+    auto kern = rot ? (merged ? k_xpass_df<true, true> : k_xpass_df<false, true>)
+                    : (merged ? k_xpass_df<true, false> : k_xpass_df<false, false>);
     cudaEvent_t e1 = nullptr;
     if (s->profile) {   // per-launch CUDA events, as for the complex64 passes
         while (s->ev_pool.size() < s->ev_used + 2) {
@@ -566,8 +572,8 @@ qs_status launch_xpass_df(qs_sim *s, int p, int variant, const double *rec, bool
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = s->pdl ? 1 : 0;
-    CK(s, cudaLaunchKernelEx(&cfg, kern, (float2 *)s->state[0], rec, s->rec_stride, s->n - LT, s->d_err,
-                             s->tmaps_dfh[p], s->tmaps_dfl[p], P));
+    CK(s, cudaLaunchKernelEx(&cfg, kern, (float2 *)s->state[0], rec, merged ? rec2 : rec, s->rec_stride, s->n - LT,
+                             s->d_err, s->tmaps_dfh[p], s->tmaps_dfl[p], P));
     CKL(s);
     s->launches++;
     if (s->profile) CK(s, cudaEventRecord(e1, s->stream));
@@ -592,7 +598,7 @@ qs_status df_convert(qs_sim *s, bool to_df) {
 template <typename R>
 qs_status launch_xpass(qs_sim *s, int p, int variant, const double *rec, int frame = 0,
                        const double *rec2 = nullptr, int xscale = 0) {
-    if (sizeof(R) == 8 && s->df_active) return launch_xpass_df(s, p, variant, rec, rec2 != nullptr);
+    if (sizeof(R) == 8 && s->df_active) return launch_xpass_df(s, p, variant, rec, rec2, frame, xscale);
     const PassDesc &d = s->pvar[NVAR * p + variant];
     const bool apply_z = d.apply_z != 0;
     dim3 grid((unsigned)(1ll << d.nfixed), (unsigned)s->batch);
@@ -707,7 +713,8 @@ qs_status run_op_fused(qs_sim *s, const Op *ops_b, const double *drec, size_t k 
             }
         }
     } else if (!ug) {
-        const bool tma = sizeof(R) == 4 && s->tmaps_ok && s->xpass_impl != 1;
+        // (complex128 with double-float passes: the same frame and C handling)
+        const bool tma = (sizeof(R) == 4 && s->tmaps_ok && s->xpass_impl != 1) || (sizeof(R) == 8 && s->df_active);
         for (int p = 0; p < np; ++p) {
             bool z_here = has_z && p == np - 1;
             int frame = 0;
@@ -917,8 +924,9 @@ qs_status build_records(qs_sim *s, size_t op0, size_t n, double dt, int n_steps,
     G.nA = s->nA; G.nB = s->nB; G.nXA = s->nXA; G.nXB = s->nXB;
     G.xlut_off = s->lat.gauge_higgs ? 0 : s->xlut_off;
     G.f32 = s->dtype == QS_C64;
-    // tangent records only where the tangent form can run (complex64 gauge-Higgs)
-    G.tan_off = (s->lat.gauge_higgs && s->dtype == QS_C64) ? s->tan_off : 0;
+    // tangent records only where the tangent form can run (gauge-Higgs; complex128 with
+    // double-float passes)
+    G.tan_off = (s->lat.gauge_higgs && (s->dtype == QS_C64 || s->tan_active)) ? s->tan_off : 0;
     G.nX0 = s->nX0; G.nX1 = s->nX1;
     G.dt = dt;
     long long entries = (long long)n * B * (1 + (G.tan_off ? 2 : 1) * (s->nA + 1) * (s->nB + 1) +
@@ -935,6 +943,8 @@ qs_status build_records(qs_sim *s, size_t op0, size_t n, double dt, int n_steps,
 // at least two qubit groups (passes).
 template <typename R>
 bool merged_schedule(const qs_sim *s) {
+    if (sizeof(R) == 8)
+        return s->df_active && s->xmerge && s->lat.gauge_higgs && s->passes.size() >= 2 && s->tan_active;
     return sizeof(R) == 4 && s->method == 0 && s->xmerge && s->lat.gauge_higgs && s->tmaps_ok &&
            s->xpass_impl != 1 && s->passes.size() >= 2 && s->tan_active;
 }
@@ -1038,8 +1048,8 @@ bool merged_schedule_ug(const qs_sim *s) {
 // complex128 unitary gauge, fused kernels: passes in double-float arithmetic
 template <typename R>
 bool df_schedule(const qs_sim *s) {
-    return sizeof(R) == 8 && s->method == 0 && s->c128_df && !s->lat.gauge_higgs && s->tmaps_df_ok &&
-           s->xpass_impl != 1 && s->passes.size() >= 2;
+    return sizeof(R) == 8 && s->method == 0 && s->c128_df && s->tmaps_df_ok && s->xpass_impl != 1 &&
+           s->passes.size() >= 2 && (!s->lat.gauge_higgs || s->tan_active);
 }
 
 template <typename R>
@@ -1082,7 +1092,8 @@ qs_status run_ops(qs_sim *s, const std::vector<Op> &ops, int steps_per_renorm_un
     // bounded growth before C is applied, and the scaled Z table u = 1 - C cos phi stays
     // away from 1, where rounding u would cost relative precision in C
     s->tan_active = false;
-    if (sizeof(R) == 4 && s->method == 0 && s->lat.gauge_higgs && s->tmaps_ok && s->xpass_impl != 1) {
+    const bool tma_path = sizeof(R) == 4 ? s->tmaps_ok : (s->c128_df && s->tmaps_df_ok);
+    if (s->method == 0 && s->lat.gauge_higgs && tma_path && s->xpass_impl != 1) {
         bool ok = true;
         for (const Op &o : ops) {
             const double t0 = std::tan(o.thx[0]), t1 = std::tan(o.thx[1]);
@@ -1459,8 +1470,10 @@ qs_status qs_create(int Lx, int Ly, int boundary, int form, int dtype, int batch
             for (int v = 0; v < 8; ++v)
                 cudaFuncSetAttribute(xpass_tma_kernel(nb, v & 1, (v >> 1) & 1, (v >> 2) & 1),
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes(s, nb, true));
-        cudaFuncSetAttribute(k_xpass_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df_smem_bytes(s));
-        cudaFuncSetAttribute(k_xpass_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df_smem_bytes(s));
+        cudaFuncSetAttribute(k_xpass_df<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df_smem_bytes(s));
+        cudaFuncSetAttribute(k_xpass_df<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df_smem_bytes(s));
+        cudaFuncSetAttribute(k_xpass_df<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df_smem_bytes(s));
+        cudaFuncSetAttribute(k_xpass_df<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df_smem_bytes(s));
         cudaFuncSetAttribute(k_adj_wl<3, 12, 1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(2 * (size_t)TMA_TILE_BYTES * 3 + 1024 + (size_t)s->max_lut * 8 + 3 * 256 * 8));
         for (int h = 0; h < 2; ++h) {

@@ -24,7 +24,12 @@
 // complex64 kernel (xpass_tma.cuh).  The pass applies unnormalised Walsh-Hadamard
 // butterflies on the pass's qubits (the unitary-gauge X layer H^n D_X H^n and the Z layer
 // between transforms, Sec. II), optionally the diagonal table with its scale, and (MERGED)
-// a second round of butterflies on the same qubits.
+// a second round of butterflies on the same qubits.  ROT: the gauge-Higgs form instead:
+// tangent-form rotations in the real frame phi = i^popc psi (a' = a + t b, b' = b - t a,
+// t = tan theta of the qubit's class in double-float, Eq. (8)), the Z layer from the
+// table scaled by the group's cos factors C, C alone for a group without Z layer, the
+// frame conversions on the first and last pass of a call, and (MERGED) the next factor
+// group's rotations on the same qubits.
 #pragma once
 #include "xpass_tma.cuh"
 
@@ -108,6 +113,50 @@ __device__ __forceinline__ void df_hadamard(u64 (&h)[NR], u64 (&l)[NR], unsigned
         for (int r = 0; r < NR; ++r)
             if (!((r >> k) & 1)) df_butterfly_lazy(h[r], l[r], h[r | (1 << k)], l[r | (1 << k)]);
     }
+}
+
+// t * x for a double-float scalar t = (th, th) + (tl, tl) and pair x: unnormalised
+// product (p, e), p = RN(th xh), e = its exact error plus the cross terms
+__device__ __forceinline__ void df_scale_lazy(u64 th, u64 tl, u64 xh, u64 xl, u64 &p, u64 &e) {
+    p = mul2(th, xh);
+    e = prod_err(th, xh, p);
+    e = fma2p(th, xl, e);
+    e = fma2p(tl, xh, e);
+}
+
+// tangent-form rotation of a pair, without renormalisation: a' = a + t b, b' = b - t a
+__device__ __forceinline__ void df_rot_lazy(u64 &ah, u64 &al, u64 &bh, u64 &bl, u64 th, u64 tl) {
+    u64 pb, eb, pa, ea;
+    df_scale_lazy(th, tl, bh, bl, pb, eb);
+    df_scale_lazy(th, tl, ah, al, pa, ea);
+    const u64 s = add2(ah, pb);
+    const u64 sv = sub2(s, ah);
+    const u64 es = add2(sub2(ah, sub2(s, sv)), sub2(pb, sv));
+    const u64 ls = add2(es, add2(al, eb));
+    const u64 d = sub2(bh, pa);
+    const u64 dv = sub2(d, bh);
+    const u64 ed = sub2(sub2(bh, sub2(d, dv)), add2(pa, dv));
+    const u64 ld = add2(ed, sub2(bl, ea));
+    ah = s; al = ls; bh = d; bl = ld;
+}
+
+// rotations on the register bits of mask; tc[k] = {(th, th), (tl, tl)} of bit k's class
+__device__ __forceinline__ void df_rotate(u64 (&h)[NR], u64 (&l)[NR], unsigned mask, const u64 (*tc)[2]) {
+#pragma unroll
+    for (int k = 0; k < RB; ++k) {
+        if (!((mask >> k) & 1u)) continue;
+        const u64 th = tc[k][0], tl = tc[k][1];
+#pragma unroll
+        for (int r = 0; r < NR; ++r)
+            if (!((r >> k) & 1)) df_rot_lazy(h[r], l[r], h[r | (1 << k)], l[r | (1 << k)], th, tl);
+    }
+}
+
+// v * i^k on both parts (exact)
+__device__ __forceinline__ void df_ipow(u64 &h, u64 &l, int k) {
+    const float2 a = mul_ipow(unpk(h), k), b = mul_ipow(unpk(l), k);
+    h = pk(a.x, a.y);
+    l = pk(b.x, b.y);
 }
 
 // Phase table entry in double-float, packed for the complex product
@@ -208,8 +257,9 @@ __global__ void k_df_join(double2 *__restrict__ state, long long n_amps) {
 // (high, low) by TMA into one buffer per CTA (two CTAs per SM); the next pair's load is
 // issued as soon as the current pair's last stage has been read from shared memory, and
 // both halves go back by per-thread stores from registers while that load is in flight.
-template <bool MERGED>
+template <bool MERGED, bool ROT>
 __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, const double *__restrict__ recs,
+                                                    const double *__restrict__ recs2,
                                                     int rec_stride, int tiles_shift, int *__restrict__ err_flag,
                                                     const __grid_constant__ CUtensorMap tmap_h,
                                                     const __grid_constant__ CUtensorMap tmap_l,
@@ -221,6 +271,8 @@ __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, 
     uint2 *ptab = reinterpret_cast<uint2 *>(lut + 4 * (P.apply_z ? (P.nA + 1) * (P.nB + 1) : 0));
     __shared__ uint64_t bar;
     __shared__ int s_ok;
+    __shared__ u64 s_tc[2][3][RB][2];   // ROT: per round, stage and register bit: (th, th), (tl, tl)
+    __shared__ u64 s_xs[2];             // ROT: C of the group, (Ch, Ch), (Cl, Cl)
 
     const int t = threadIdx.x;
     const long long G = gridDim.x;
@@ -289,10 +341,28 @@ __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, 
         if (batch != cur_batch) {
             // phase table of this batch element: (cos, sin) in double-float, packed
             __syncthreads();
+            const double *rec = recs + batch * rec_stride;
+            if (ROT && t < 2 * 3 * RB) {
+                // round 0: this factor group (stages A, B, C); round 1 (MERGED): the next one
+                const int round = t / (3 * RB), st = (t / RB) % 3, k = t % RB;
+                if (round == 0 || MERGED) {
+                    const double *rr = round ? recs2 + batch * rec_stride : rec;
+                    const double tv = rr[P.tan_off + ((P.cls[st] >> k) & 1)];
+                    const float a = __double2float_rn(tv), b = __double2float_rn(tv - (double)a);
+                    s_tc[round][st][k][0] = pk(a, a);
+                    s_tc[round][st][k][1] = pk(b, b);
+                }
+            }
+            if (ROT && t == 0) {
+                const double cv = rec[P.tan_off + 2];
+                const float a = __double2float_rn(cv), b = __double2float_rn(cv - (double)a);
+                s_xs[0] = pk(a, a);
+                s_xs[1] = pk(b, b);
+            }
             if (P.apply_z) {
-                const double *rec = recs + batch * rec_stride;
+                const int loff = ROT ? P.tan_off + 4 : P.lut_off;   // ROT: the table scaled by C
                 for (int i = t; i < nlut; i += NT) {
-                    const double c = 1.0 - rec[P.lut_off + 2 * i], s = rec[P.lut_off + 2 * i + 1];
+                    const double c = 1.0 - rec[loff + 2 * i], s = rec[loff + 2 * i + 1];
                     const float ch = __double2float_rn(c), cl = __double2float_rn(c - (double)ch);
                     const float sh = __double2float_rn(s), sl = __double2float_rn(s - (double)sh);
                     u64 *q = lut + 4 * i;
@@ -317,7 +387,13 @@ __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, 
         // ---- stage A: registers = local 8..11 ----
 #pragma unroll
         for (int r = 0; r < NR; ++r) { h[r] = th[a_base + (r << TB)]; l[r] = tl[a_base + (r << TB)]; }
-        df_hadamard(h, l, P.rot[0]);
+        const int pc_tile = __popcll(tile & tmask);
+        if (ROT && (P.frame & 2)) {   // psi -> phi = i^popc psi
+            const int k0 = __popc(t) + pc_tile;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) df_ipow(h[r], l[r], k0 + __popc(r));
+        }
+        if (ROT) df_rotate(h, l, P.rot[0], s_tc[0][0]); else df_hadamard(h, l, P.rot[0]);
 #pragma unroll
         for (int r = 0; r < NR; ++r) { th[a_base + (r << TB)] = h[r]; tl[a_base + (r << TB)] = l[r]; }
         __syncthreads();
@@ -330,7 +406,7 @@ __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, 
                 h[2 * m] = qh.x; h[2 * m + 1] = qh.y;
                 l[2 * m] = ql.x; l[2 * m + 1] = ql.y;
             }
-            df_hadamard(h, l, P.rot[1]);
+            if (ROT) df_rotate(h, l, P.rot[1], s_tc[0][1]); else df_hadamard(h, l, P.rot[1]);
 #pragma unroll
             for (int m = 0; m < NR / 2; ++m) {
                 th2[b_base + (m ^ b_x)] = make_ulonglong2(h[2 * m], h[2 * m + 1]);
@@ -346,7 +422,7 @@ __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, 
             __syncthreads();
             if (t == 0 && it + 1 < n_my) issue(tile + G);
         }
-        df_hadamard(h, l, P.rot[2]);
+        if (ROT) df_rotate(h, l, P.rot[2], s_tc[0][2]); else df_hadamard(h, l, P.rot[2]);
         const long long mid = tile & ((1ll << P.mid_bits) - 1);
         const long long up = tile >> P.mid_bits;
         const long long gbase = (mid << P.c) + (up << (P.next + P.k));
@@ -368,10 +444,24 @@ __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, 
                 for (int r = 0; r < NR; ++r) { h[r] = mul2(h[r], dscale); l[r] = mul2(l[r], dscale); }
             }
         }
+        if (ROT && !P.apply_z && P.xscale) {   // C of a factor group without Z layer
+            const u64 ch = s_xs[0], cl = s_xs[1];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                u64 p, e;
+                df_scale_lazy(ch, cl, h[r], l[r], p, e);
+                h[r] = p; l[r] = e;
+            }
+        }
+        if (ROT && !MERGED && (P.frame & 4)) {   // phi -> psi
+            const int k0 = -(__popc(tlo) + __popc(thi) + pc_tile);
+#pragma unroll
+            for (int r = 0; r < NR; ++r) df_ipow(h[r], l[r], (k0 - __popc(r)) & 3);
+        }
         u64 *dst;
         if (MERGED) {
             // ---- second round: stage C (in registers), B, A; store from stage A ----
-            df_hadamard(h, l, P.rot[2]);
+            if (ROT) df_rotate(h, l, P.rot[2], s_tc[1][2]); else df_hadamard(h, l, P.rot[2]);
 #pragma unroll
             for (int r = 0; r < NR; ++r) { th[c_base[r & 7] + (r << 4)] = h[r]; tl[c_base[r & 7] + (r << 4)] = l[r]; }
             __syncthreads();
@@ -383,7 +473,7 @@ __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, 
                     h[2 * m] = qh.x; h[2 * m + 1] = qh.y;
                     l[2 * m] = ql.x; l[2 * m + 1] = ql.y;
                 }
-                df_hadamard(h, l, P.rot[1]);
+                if (ROT) df_rotate(h, l, P.rot[1], s_tc[1][1]); else df_hadamard(h, l, P.rot[1]);
 #pragma unroll
                 for (int m = 0; m < NR / 2; ++m) {
                     th2[b_base + (m ^ b_x)] = make_ulonglong2(h[2 * m], h[2 * m + 1]);
@@ -395,7 +485,12 @@ __global__ void __launch_bounds__(NT, 2) k_xpass_df(float2 *__restrict__ state, 
             for (int r = 0; r < NR; ++r) { h[r] = th[a_base + (r << TB)]; l[r] = tl[a_base + (r << TB)]; }
             __syncthreads();
             if (t == 0 && it + 1 < n_my) issue(tile + G);
-            df_hadamard(h, l, P.rot[0]);
+            if (ROT) df_rotate(h, l, P.rot[0], s_tc[1][0]); else df_hadamard(h, l, P.rot[0]);
+            if (ROT && (P.frame & 4)) {   // phi -> psi
+                const int k0 = -(__popc(t) + pc_tile);
+#pragma unroll
+                for (int r = 0; r < NR; ++r) df_ipow(h[r], l[r], (k0 - __popc(r)) & 3);
+            }
             df_renorm(h, l);
             // blocked layout: amplitude g = 16 m + j has its high pair at float2 index
             // 32 m + j and its low pair at 32 m + 16 + j

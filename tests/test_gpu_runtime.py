@@ -52,30 +52,39 @@ def test_renormalisation_keeps_unit_norm_and_the_state():
 
 
 @gpu
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("dtype", ["c64", "c128", "c128-df"])
 def test_checkpoint_resume_is_bit_identical(tmp_path, dtype):
     """Save after 9 of 20 first-order steps, load into a new simulator, finish: the
     state is bit-identical to the same two calls without the checkpoint.  Splitting
-    the run into two calls is itself exact with separate passes (complex128 here);
-    with shared passes (complex64) the first X factors of the second call meet their
-    qubit groups in another order, which changes rounding only."""
-    from paper_2108_13410_gb300.qsim import QS_OPT_XMERGE
+    the run into two calls is itself exact with separate FP64 passes (complex128 with
+    QS_OPT_C128_DF 0); with shared passes (complex64, and complex128 in double-float
+    passes, which also convert the layout at every call boundary) the first X factors
+    of the second call meet their qubit groups in another order, which changes
+    rounding only."""
+    from paper_2108_13410_gb300.qsim import QS_OPT_XMERGE, QS_OPT_C128_DF
     T, n = 2.0, 20
     s = O.schedule_linear(T, n)
     cpl = [(0.6, 0.6)]
-    full = _sim(3, 2, form="gh", dtype=dtype)
+    dt = "c64" if dtype == "c64" else "c128"
+
+    def mk():
+        sim = _sim(3, 2, form="gh", dtype=dt)
+        if dtype == "c128":
+            sim.set_option(QS_OPT_C128_DF, 0)
+        return sim
+    full = mk()
     full.init_plus()
     full.evolve(cpl, s, T / n, 1)
-    two = _sim(3, 2, form="gh", dtype=dtype)
+    two = mk()
     two.init_plus()
     two.evolve(cpl, s[:9], T / n, 1)
     two.evolve(cpl, s[9:], T / n, 1)
-    part = _sim(3, 2, form="gh", dtype=dtype)
+    part = mk()
     part.init_plus()
     part.evolve(cpl, s[:9], T / n, 1)
     path = str(tmp_path / "ckpt.qs")
     part.save(path)
-    resumed = _sim(3, 2, form="gh", dtype=dtype)
+    resumed = mk()
     resumed.load(path)
     resumed.evolve(cpl, s[9:], T / n, 1)
     assert np.array_equal(two.download().numpy(), resumed.download().numpy())
@@ -83,6 +92,8 @@ def test_checkpoint_resume_is_bit_identical(tmp_path, dtype):
     b = resumed.download().numpy().astype(np.complex128)
     if dtype == "c128":
         assert np.array_equal(a, b)
+    elif dtype == "c128-df":
+        assert np.linalg.norm(a - b) <= 1e-13
     else:
         assert np.linalg.norm(a - b) <= 1e-6
         # separate passes: the split is exact in complex64 too
