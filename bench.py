@@ -372,6 +372,25 @@ def run_ours(args):
                                  "fused_c64_speedup": value / world / pg}
         del sp
         torch.cuda.empty_cache()
+        # the fused complex128 passes (the paper's precision): double-float arithmetic
+        # (default) and FP64, each over one call of kf steps
+        from paper_2108_13410_gb300.qsim import QS_OPT_C128_DF
+        fused = {}
+        for name, df, kf in (("double_float", 1, 40), ("fp64", 0, 10)):
+            sf = Simulator(W["Lx"], W["Ly"], form=W["form"], dtype="c128", device=f"cuda:{local}")
+            sf.set_option(QS_OPT_C128_DF, df)
+            sf.init_plus()
+            sf.evolve(cpl, sched[:3], dt, W["order"])
+            torch.cuda.synchronize(dev)
+            a0.record(stream)
+            sf.evolve(cpl, sched[3:3 + kf], dt, W["order"])
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            fused[name] = {"value": kf / (a0.elapsed_time(a1) / 1000.0), "unit": UNIT, "steps": kf}
+            del sf
+            torch.cuda.empty_cache()
+        fused["double_float"]["over_pergate"] = fused["double_float"]["value"] / pg
+        extra["fused_c128"] = fused
 
     if rank == 0 and not args.no_accuracy:
         extra["accuracy"] = accuracy_leg(local, dev)
