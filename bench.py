@@ -633,8 +633,13 @@ def adjoint_leg(n_steps, local, dev, stream):
     cpl = [(W["g"], W["lam"])]
     out = {"steps": n_steps, "M": 16, "T": T}
     grads = {}
+    from paper_2108_13410_gb300.qsim import QS_OPT_C128_DF
     for dtype in ("c64", "c128"):
         sim = Simulator(W["Lx"], W["Ly"], form=W["form"], dtype=dtype, device=f"cuda:{local}", aux=True)
+        if dtype == "c128":
+            # the reference: FP64 forward and FP64 reverse sweep (the reverse passes have
+            # no double-float form)
+            sim.set_option(QS_OPT_C128_DF, 0)
         sim.init_plus()
         sim.evolve(cpl, s[:3], dt, 2)
         torch.cuda.synchronize(dev)
@@ -654,6 +659,8 @@ def adjoint_leg(n_steps, local, dev, stream):
         grads[dtype] = jac @ g[0]
         out[dtype] = {"forward_ms": fwd_ms, "adjoint_ms": adj_ms, "adjoint_over_forward": adj_ms / fwd_ms,
                       "energy": float(val[0])}
+        if dtype == "c128":
+            out[dtype]["arithmetic"] = "FP64"
         del sim
         torch.cuda.empty_cache()
     ref = grads["c128"]
