@@ -1878,7 +1878,6 @@ qs_status qs_scan(qs_sim *s, const qs_couplings *points, int n_points, const dou
     if (!points || !sv || !out) FAIL(s, QS_ERR_ARG, "null argument");
     if (n_points < 1 || n_steps < 1) FAIL(s, QS_ERR_ARG, "n_points and n_steps must be >= 1");
     if (order != 1 && order != 2) FAIL(s, QS_ERR_ARG, "order must be 1 or 2");
-    const int nops = order == 2 ? n_steps + 1 : n_steps;
     if (s->n == LT && s->lat.gauge_higgs && s->nA + s->nB + 2 <= 64) {
         // ---- every point in one persistent launch, state in shared memory ----
         size_t in_doubles = (size_t)n_points * 4 + (size_t)n_steps;
