@@ -168,3 +168,23 @@ def test_27_qubit_gauge_higgs_slice_matches_unitary_gauge_oracle():
     assert rel <= 1e-10 and mx <= 1e-10, (rel, mx)
     del sim
     torch.cuda.empty_cache()
+
+
+@gpu
+@pytest.mark.parametrize("lattice,form", [((2, 2), "gh"), ((3, 2), "ug"), ((4, 2), "ug")],
+                         ids=["gh2x2open-21q", "ug3x2open-17q", "ug4x2open-22q"])
+def test_open_lattices(lattice, form):
+    """Open lattices with edge pass plans (12 + 8 + 1, 12 + 5, 12 + 8 + 2) in complex128
+    double-float passes: oracle parity at 1e-10."""
+    from paper_2108_13410_gb300 import Simulator
+    Lx, Ly = lattice
+    lat = OracleLattice(Lx, Ly, False, form)
+    n_steps = 3
+    T = 0.15 * n_steps
+    s = O.schedule_linear(T, n_steps)
+    ref = O.evolve(lat, Couplings(0.7, 0.4), s, T / n_steps, 2)
+    sim = Simulator(Lx, Ly, form=form, dtype="c128", boundary="open")
+    sim.init_plus()
+    sim.evolve([(0.7, 0.4)], s, T / n_steps, 2)
+    rel, mx = _rel(sim.download()[0].numpy(), ref)
+    assert rel <= 1e-10 and mx <= 1e-10, (rel, mx)

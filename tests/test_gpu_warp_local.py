@@ -205,3 +205,32 @@ def test_27_qubit_shared_reverse_passes_agree():
         torch.cuda.empty_cache()
     assert res[0][0] == res[1][0]
     assert np.max(np.abs(res[0][1] - res[1][1])) <= 1e-5 * np.max(np.abs(res[1][1]))
+
+
+@gpu
+@pytest.mark.parametrize("lattice,form", [((2, 2), "gh"), ((3, 2), "ug"), ((4, 2), "ug")],
+                         ids=["gh2x2open-21q", "ug3x2open-17q", "ug4x2open-22q"])
+def test_open_lattices_edge_passes(lattice, form):
+    """Open lattices whose shared passes are edge cases of the slice split: 21 qubits
+    (gauge-Higgs, plan 12 + 8 + 1: a pass rotating tile bit 11 alone), 17 qubits (unitary
+    gauge, 12 + 5: 32 tiles for 152 CTAs, most of which get no tile) and 22 qubits
+    (unitary gauge, 12 + 8 + 2).  Oracle parity and bit-identity with the CTA-staged
+    kernel."""
+    from paper_2108_13410_gb300 import Simulator
+    from paper_2108_13410_gb300.qsim import QS_OPT_SHARED_KERNEL
+    Lx, Ly = lattice
+    lat = OracleLattice(Lx, Ly, False, form)
+    n_steps = 3
+    T = 0.15 * n_steps
+    s = O.schedule_linear(T, n_steps)
+    ref = O.evolve(lat, Couplings(0.7, 0.4), s, T / n_steps, 2)
+    out = []
+    for kern in (1, 0):
+        sim = Simulator(Lx, Ly, form=form, dtype="c64", boundary="open")
+        sim.set_option(QS_OPT_SHARED_KERNEL, kern)
+        sim.init_plus()
+        sim.evolve([(0.7, 0.4)], s, T / n_steps, 2)
+        out.append(sim.download()[0].numpy())
+    rel, mx = _rel(out[0], ref)
+    assert rel <= 1e-5 and mx <= 1e-5, (rel, mx)
+    assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
