@@ -86,7 +86,7 @@ def test_adjoint_over_more_than_one_record_chunk():
 @gpu
 def test_hysteresis_run_complex64_matches_complex128():
     """The hysteresis protocol of Sec. IV at p = 0.5 with a coarser dg = 5e-4 (1000 +
-    1000 steps per state): complex64 with renormalisation every 100 steps (the driver's
+    1000 steps per state): complex64 with renormalisation every 100 steps (the protocol's
     default) gives the complex128 energies to 5e-6 along both curves; E and E' (both
     read at P) lie above the ground energy of the 3x3 unitary-gauge torus at (0.5, 0),
     which is below -14.0656."""
