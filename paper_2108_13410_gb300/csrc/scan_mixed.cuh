@@ -123,6 +123,71 @@ __device__ void ug_tile(u64 *tb, const TmaPass &P, uint32_t pa, uint32_t pb, con
     for (int r = 0; r < NR; ++r) tb[a_base + (r << TB)] = w[r];
 }
 
+// The same for a pass whose butterflies sit on tile bits 8..11 and 7 only (the 17-qubit
+// lattice's second pass, 5 new qubits): one layout L holds the whole round, registers =
+// bits 8..11, lanes = bits 0..3 and 7, warps = bits 4..6.  Bit 7's butterflies exchange
+// through a warp shuffle (partner lane ^ 16), so the tile is read and written once, with
+// no block barrier inside the tile.  With the 128-byte swizzle a half-warp reads one whole
+// 128-byte row (bits 0..3), free of bank conflicts.  pa, pb: parity words of the tile.
+__device__ void ug_tile_l(u64 *tb, const TmaPass &P, uint32_t pa, uint32_t pb, const DiagOps &D, bool round2,
+                          float (&m)[3]) {
+    const int t = threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    // slot of register r: l = (lane & 15) | warp << 4 | (lane >> 4) << 7 | r << 8,
+    // swizzled l ^ (((l >> 4) & 7) << 1) = l ^ (warp << 1)
+    const int base = ((lane & 15) ^ (warp << 1)) | (warp << 4) | ((lane >> 4) << 7);
+    // parity of this thread's local bits (0..3 and 7 from the lane, 4..6 from the warp)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if ((lane >> j) & 1) { pa ^= P.paA_thr[j]; pb ^= P.pbA_thr[j]; }
+    if (lane & 16) { pa ^= P.paA_thr[7]; pb ^= P.pbA_thr[7]; }
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        if ((warp >> j) & 1) { pa ^= P.paA_thr[4 + j]; pb ^= P.pbA_thr[4 + j]; }
+    const bool bit7 = (P.rot[2] & 8u) != 0;
+    const float sg = (lane & 16) ? -1.f : 1.f;
+    const u64 sgn = pk(sg, sg);
+    // butterflies on bit 7: the lane with the bit clear keeps self + partner, the other
+    // partner - self
+    auto shfl_round = [&](u64 (&w)[NR]) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const unsigned lo = (unsigned)w[r], hi = (unsigned)(w[r] >> 32);
+            const u64 other = ((u64)__shfl_xor_sync(0xffffffffu, hi, 16) << 32) | __shfl_xor_sync(0xffffffffu, lo, 16);
+            w[r] = fma2p(sgn, w[r], other);
+        }
+    };
+    u64 w[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) w[r] = tb[base + (r << 8)];
+    had_w(w, P.rot[0]);
+    if (bit7) shfl_round(w);
+    if (D.ta || D.measure) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int oa = __popc(pa ^ P.paA_reg[r]), ob = __popc(pb ^ P.pbA_reg[r]);
+            float2 v = unpk(w[r]);
+            if (D.ta) {
+                v = cphase(cphase(v, D.ta[oa]), D.tb[ob]);
+                v.x *= D.scale; v.y *= D.scale;
+            }
+            if (D.measure) {
+                const float q = (v.x * v.x + v.y * v.y) * D.wscale;
+                m[0] += q;
+                m[1] += q * (float)(P.nA - 2 * oa);
+                m[2] += q * (float)(P.nB - 2 * ob);
+            }
+            w[r] = pk(v.x, v.y);
+        }
+    }
+    if (round2) {
+        if (bit7) shfl_round(w);
+        had_w(w, P.rot[0]);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) tb[base + (r << 8)] = w[r];
+}
+
 // Persistent scan of both lattices.  Shared memory (dynamic, 1024-byte aligned): NBUF
 // 32 KB tile buffers (the 12-qubit points use the first as their state); a pass keeps
 // NBUF - 1 tile loads in flight ahead of the tile being processed.
@@ -213,7 +278,8 @@ __global__ void __launch_bounds__(NT, NBUF <= 3 ? 2 : 1) k_scan_mixed(const DevC
             u64 *tb = reinterpret_cast<u64 *>(buf + (size_t)b * (1 << LT));
             uint32_t pa, pb;
             tile_par(P, tt, pa, pb);
-            ug_tile(tb, P, pa ^ pa_t, pb ^ pb_t, D, round2, m);
+            if (P.rot[1] == 0 && (P.rot[2] & ~8u) == 0) ug_tile_l(tb, P, pa, pb, D, round2, m);
+            else ug_tile(tb, P, pa ^ pa_t, pb ^ pb_t, D, round2, m);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
             if (store && t == 0) {
