@@ -543,7 +543,9 @@ def ug32_leg(local, dev, stream):
            "dt": 0.02, "order": 2}
     from paper_2108_13410_gb300.qsim import QS_OPT_C128_DF
     # complex128: the double-float passes (default) and the FP64 register kernel
-    for key, dtype, n, df in (("c64", "c64", 10, 1), ("c128", "c128", 10, 1), ("c128_fp64", "c128", 2, 0)):
+    # one call of n steps each (the schedule's 1000 steps run as one call; every call adds
+    # the passes of its first and last factor groups)
+    for key, dtype, n, df in (("c64", "c64", 30, 1), ("c128", "c128", 20, 1), ("c128_fp64", "c128", 2, 0)):
         sim = Simulator(4, 4, form="ug", dtype=dtype, device=f"cuda:{local}")
         if dtype == "c128":
             sim.set_option(QS_OPT_C128_DF, df)
