@@ -215,6 +215,49 @@ __global__ void __launch_bounds__(32 * NW, MINB) k_xpass_wl(float2 *__restrict__
                     v[r] = pk(x.x, x.y);
                 }
             }
+            if (P.rot[2] == 0) {
+                // every rotated qubit on tile bits 8..11: both rounds and the Z layer in
+                // layout L1, each lane writing back the slots it read (no exchange)
+                if (HAD) hadamard_w(v, P.rot[0]); else rotate_ts(v, P.rot[0], s_tc[0][0]);
+                const uint2 e0 = ptab[tile & 255], e1 = ptab[256 + ((tile >> 8) & 255)],
+                            e2 = ptab[512 + ((tile >> 16) & 255)];
+                uint32_t pa = e0.x ^ e1.x ^ e2.x, pb = e0.y ^ e1.y ^ e2.y;
+                if (l0) { pa ^= P.paA_thr[0]; pb ^= P.pbA_thr[0]; }
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    if ((w >> q) & 1) { pa ^= P.paA_thr[1 + q]; pb ^= P.pbA_thr[1 + q]; }
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if ((lh >> q) & 1) { pa ^= P.paA_thr[4 + q]; pb ^= P.pbA_thr[4 + q]; }
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    const float2 x = cphase(unpk(v[r]), lut[__popc(pa ^ P.paA_reg[r]) * nB1 + __popc(pb ^ P.pbA_reg[r])]);
+                    v[r] = pk(x.x, x.y);
+                }
+                if (P.scale != 1.0f) {
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        float2 x = unpk(v[r]);
+                        x.x *= P.scale; x.y *= P.scale;
+                        v[r] = pk(x.x, x.y);
+                    }
+                }
+                if (HAD) hadamard_w(v, P.rot[0]); else rotate_ts(v, P.rot[0], s_tc[1][0]);
+                if (P.frame & 4) {
+                    const int k0 = -(__popc(lane) + __popc(w) + pc_tile);
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const float2 x = mul_ipow(unpk(v[r]), (k0 - __popc(r)) & 3);
+                        v[r] = pk(x.x, x.y);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < NR; ++r) *reinterpret_cast<u64 *>(tb + base_t + (r << 11)) = v[r];
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&done[b]);
+                continue;
+            }
             if (HAD) hadamard_w(v, P.rot[0]); else rotate_ts(v, P.rot[0], s_tc[0][0]);
             __syncwarp();
 #pragma unroll
