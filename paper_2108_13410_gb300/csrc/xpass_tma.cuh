@@ -415,7 +415,6 @@ __global__ void __launch_bounds__(NT, NBUF == 2 ? 3 : 2) k_xpass_tma(float2 *__r
     }
     const int nB1 = P.nB + 1;
     const int nlut = (P.nA + 1) * nB1;
-    const bool had = P.hadamard != 0;
     long long cur_batch = -1;
     XC RC;
     float xs = 1.f;                                   // tangent form: scalar C of the record
